@@ -1,0 +1,191 @@
+/*
+ * rgx.h -- C ABI of librgx: differentiable volume ray marching through
+ * truncated elliptical Gaussians on one NVIDIA B300 (sm_103a).
+ *
+ * Method: RayGaussX (arXiv 2509.07782).  The density and radiance fields are
+ * sums of Gaussians (Eq. 1); a ray is integrated front to back in segments of
+ * N_S samples (Eq. 3, Algorithm 1) with empty-space skipping through a BVH
+ * ClosestHit query (Algorithm 1, Eq. 4), a distance- and transmittance-
+ * adaptive segment size (Eq. 5), early termination at T <= T_eps, Gaussians
+ * stored in Z-order (Sec. 3.3) and rays grouped in 2D tiles (Sec. 3.3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Array arguments are DEVICE pointers owned by the caller: contiguous,
+ *    float32 unless stated, on the scene's device.  Camera arrays are HOST
+ *    pointers (pinned memory is best: they are copied with cudaMemcpyAsync).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Every call only enqueues work on it and returns; no
+ *    call synchronises except rgx_sync_status.
+ *  - Every call returns an rgx_status.  No C++ exception crosses the ABI.
+ *    rgx_last_error() gives a static description of the last failure.
+ *  - Problems found on the device (segment limit reached, traversal stack
+ *    overflow, bad parameters such as s <= 0 or NaN) are OR-ed into a device
+ *    status word held by the scene; rgx_sync_status() synchronises the stream
+ *    and returns (and clears) it.  Kernels never trap and never spin without
+ *    a bound.
+ *  - A scene owns its workspace (BVH, Z-order permutation, packed
+ *    parameters, gradient accumulators).  It grows on demand inside
+ *    rgx_build_bvh / rgx_render_*; once a scene has seen the largest sizes it
+ *    will be used with, later calls allocate nothing and can be captured in a
+ *    CUDA graph.
+ *  - Calls on one scene must not overlap in time (one stream per scene).
+ */
+#ifndef RGX_H
+#define RGX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rgx_status;
+#define RGX_OK                  0
+#define RGX_ERR_INVALID_ARG     1   /* bad pointer, size or option (host check) */
+#define RGX_ERR_CUDA            2   /* a CUDA runtime call failed */
+#define RGX_ERR_WORKSPACE       3   /* device allocation failed */
+#define RGX_ERR_HIT_OVERFLOW    4   /* reserved: hit lists are chunked, never dropped */
+#define RGX_ERR_STACK_OVERFLOW  8   /* device: BVH deeper than the traversal stack */
+#define RGX_ERR_ITER_LIMIT      16  /* device: a ray reached max_segments */
+#define RGX_ERR_BAD_PARAMS      32  /* device: NaN/Inf parameter, scale <= 0, |q| = 0 */
+#define RGX_ERR_REPLAY          64  /* device: backward replay did not reproduce T_final */
+#define RGX_ERR_NOT_BUILT       128 /* render called before rgx_build_bvh */
+
+/* option flags (rgx_opts.flags) */
+#define RGX_SKIP      1    /* empty-space skipping: Algorithm 1 ClosestHit, Eq. 4 */
+#define RGX_ADAPTIVE  2    /* Eq. 5 segment size instead of uniform dt */
+#define RGX_MORTON    4    /* store packed parameters in Z-order (Sec. 3.3) */
+#define RGX_ZTILES    8    /* 2D ray tiles in Z-order instead of scanline warps (Sec. 3.3) */
+#define RGX_MORTON63  16   /* 63-bit (21 bits/axis) instead of 30-bit Morton codes */
+
+typedef struct rgx_scene rgx_scene;   /* opaque */
+
+/* Pinhole camera, OpenCV convention (+z forward, +y down).  Pixel (u, v)
+ * looks along c2w[:, :3] ((u+0.5-cx)/fx, (v+0.5-cy)/fy, 1), normalised; the
+ * ray starts at the camera centre c2w[:, 3].  t_far <= 0 means "exit of the
+ * scene bounding box" (the union of all ellipsoid AABBs). */
+typedef struct {
+    float c2w[12];               /* row-major 3x4 camera-to-world */
+    float fx, fy, cx, cy;        /* intrinsics in pixels */
+    int32_t width, height;
+    float t_near, t_far;         /* integration bounds t_n, t_f of Algorithm 1 */
+} rgx_camera;
+
+/* Marching options: the inputs of Algorithm 1 and Eq. 5. */
+typedef struct {
+    int32_t flags;               /* RGX_SKIP | RGX_ADAPTIVE | RGX_MORTON | RGX_ZTILES | RGX_MORTON63 */
+    float dt;                    /* uniform step (Eq. 3) */
+    float dt_min, dt_max, beta;  /* Eq. 5 parameters */
+    int32_t n_s;                 /* samples per segment N_S: 4, 8, 16 or 32 */
+    float t_eps;                 /* transmittance threshold T_eps (Algorithm 1) */
+    float sigma_eps;             /* truncation density: support is sigma(x) >= sigma_eps */
+    float bg[3];                 /* background colour, added as T_final * bg */
+    int32_t tile_w, tile_h;      /* ray tile, tile_w * tile_h == 32 (ZTILES only) */
+    int32_t hit_cap;             /* hit-list chunk per ray (8..256); never drops hits */
+    int32_t max_segments;        /* loop bound per ray; 0 = derived from the ray length */
+} rgx_opts;
+
+/* Create / destroy a scene handle bound to CUDA device `device`. */
+rgx_status rgx_scene_create(rgx_scene** out, int32_t device);
+rgx_status rgx_scene_destroy(rgx_scene* scene);
+
+/*
+ * Build the acceleration structure and packed parameters for n Gaussians.
+ * Sec. 3.2 ("the structure is updated at each optimization step") and Sec.
+ * 3.3 (Z-order re-indexing); ellipsoid AABB from Supp. Sec. 2.2.
+ *
+ *   means      [n,3]            Gaussian means mu
+ *   scales     [n,3]            linear scales s > 0 (Sigma = R S S^T R^T)
+ *   quats      [n,4]            rotations as (w,x,y,z); normalised here
+ *   densities  [n]              sigma~ (peak density); sigma~ <= sigma_eps
+ *                               gives an empty support
+ *   sh         [n,(deg+1)^2,3]  SH coefficients, channel fastest
+ *   sh_degree  0..3
+ *
+ * Steps (all on `stream`): scene bounds of the means, 30/63-bit Morton codes,
+ * LSD radix sort of (code, index), Karras radix tree, bottom-up AABB refit,
+ * and packing of the parameters into float4 records (in Z-order with
+ * RGX_MORTON, else in caller order).  The arrays are read during this call
+ * only; the scene keeps its own packed copy.  n may be 0.
+ */
+rgx_status rgx_build_bvh(rgx_scene* scene, int64_t n, int32_t sh_degree,
+                         const float* means, const float* scales, const float* quats,
+                         const float* densities, const float* sh,
+                         const rgx_opts* opts, void* stream);
+
+/*
+ * Forward render of ncam cameras in one persistent launch (Algorithm 1 for
+ * every pixel; Eq. 1 densities and SH colours; Eq. 3 compositing).
+ *
+ *   cams       HOST [ncam]  cameras (copied on `stream`)
+ *   rgba       [R,4]        output, R = sum_c width_c*height_c, camera-major,
+ *                           row-major pixels: (C + T bg, 1 - T)
+ *   fwd_state  [R] x rgx_fwd_state_bytes()  per-ray (C, T) kept for the adjoint
+ *                           (may be NULL for inference)
+ */
+rgx_status rgx_render_forward(rgx_scene* scene, const rgx_camera* cams, int32_t ncam,
+                              const rgx_opts* opts, float* rgba, void* fwd_state, void* stream);
+
+/*
+ * Same as rgx_render_forward, and also records each ray's evaluated segments
+ * (t_S, dt) -- the schedule -- into sched [R, sched_cap, 2] with the count per
+ * ray in sched_n [R] (int32; counts beyond sched_cap are still counted).
+ * Used to check discrete decisions against a reference.
+ */
+rgx_status rgx_render_forward_sched(rgx_scene* scene, const rgx_camera* cams, int32_t ncam,
+                                    const rgx_opts* opts, float* rgba, void* fwd_state,
+                                    float* sched, int32_t sched_cap, int32_t* sched_n, void* stream);
+
+/*
+ * Adjoint of rgx_render_forward: replays each ray's march front to back
+ * (recomputing, not storing, per-sample densities) and ACCUMULATES (+=)
+ * dL/d{means, scales, quats, densities, sh} in the caller's order for the
+ * upstream gradient d_rgba [R,4].  Gradients are for the raw inputs of
+ * rgx_build_bvh (linear scales, unnormalised quaternions).  The truncation
+ * boundary, the schedule and termination are held fixed (piecewise
+ * constant).  Rays whose d_rgba row is zero contribute nothing and are
+ * skipped.  Must follow rgx_render_forward with the same cameras and options
+ * on a scene not rebuilt in between.
+ */
+rgx_status rgx_render_backward(rgx_scene* scene, const rgx_camera* cams, int32_t ncam,
+                               const rgx_opts* opts, const void* fwd_state, const float* d_rgba,
+                               float* d_means, float* d_scales, float* d_quats,
+                               float* d_densities, float* d_sh, void* stream);
+
+/* Synchronise `stream`, return the device status word (RGX_ERR_* bits, 0 if
+ * clean) and clear it. */
+rgx_status rgx_sync_status(rgx_scene* scene, void* stream);
+
+/* Bytes of per-ray state written by rgx_render_forward (16: C[3], T). */
+size_t rgx_fwd_state_bytes(void);
+
+/* Static description of the last error on this scene (or globally if NULL). */
+const char* rgx_last_error(const rgx_scene* scene);
+
+/*
+ * Introspection for tests (device output pointers, enqueued on `stream`):
+ *   codes  [n]   sorted Morton codes (uint64)
+ *   perm   [n]   sorted position -> caller index (int32)
+ *   nodes  [max(n-1,1), 16] internal nodes: left lo/hi, right lo/hi boxes and
+ *                (first, split, last) leaf ranges as int32 bit patterns at
+ *                floats 3, 7, 11
+ *   root   [6]   scene box (lo xyz, hi xyz)
+ * Any pointer may be NULL.
+ */
+rgx_status rgx_get_bvh(rgx_scene* scene, uint64_t* codes, int32_t* perm, float* nodes,
+                       float* root, void* stream);
+
+/*
+ * Work counters of the last forward or backward call (HOST output, 8 x
+ * uint64; synchronises the stream): [0] rays, [1] evaluated segments,
+ * [2] (ray, segment, Gaussian) hits, [3] (sample, Gaussian) evaluations,
+ * [4] BVH node visits, [5] ClosestHit queries, [6] skipped segments, [7] 0.
+ */
+rgx_status rgx_get_counters(rgx_scene* scene, uint64_t* out8, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RGX_H */

@@ -1,0 +1,118 @@
+// common.cuh -- internal declarations of librgx (not part of the ABI).
+//
+// Packed per-Gaussian record (packed index p; Z-order position with
+// RGX_MORTON, caller index otherwise):
+//   geom[4p+0] = (mu.x, mu.y, mu.z, Q_eps)       Q_eps = 2 ln(sigma~/sigma_eps)
+//   geom[4p+1] = (M00, M01, M02, log2 sigma~)    M = S^-1 R^T (whitening)
+//   geom[4p+2] = (M10, M11, M12, sigma~)
+//   geom[4p+3] = (M20, M21, M22, 0)
+//   shc [12p..12p+11] = 48 SH coefficients, (k, channel) channel fastest
+//   aux [2p+0] = raw quaternion (w,x,y,z), aux[2p+1] = (s0, s1, s2, 0)
+// so that q(x) = |M (x - mu)|^2 and sigma_l(x) = sigma~ exp(-q/2) (Supp. Sec. 2.1).
+//
+// Internal BVH node i (0 <= i < n-1), 4 x float4 = 64 B, both children's
+// boxes stored in the parent so one fetch tests both:
+//   node[4i+0] = (left.lo xyz,  first)   first/split/last: int32 bit patterns
+//   node[4i+1] = (left.hi xyz,  split)   left child  = split   (leaf iff first == split)
+//   node[4i+2] = (right.lo xyz, last)    right child = split+1 (leaf iff split+1 == last)
+//   node[4i+3] = (right.hi xyz, 0)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+#include "../../include/rgx.h"
+
+#define RGX_STACK 96          // >= depth of a radix tree over (63-bit code, 32-bit index) keys
+#define RGX_MAX_CAMS 1024
+#define RGX_BLOCK 128         // threads per block of the march kernels
+
+// ---------------------------------------------------------------- scene
+struct rgx_scene {
+    int device = 0;
+    int num_sms = 0;
+    // current build
+    int64_t n = 0;
+    int sh_degree = 0;
+    int built = 0;
+    int morton = 0;           // packed order is Z-order
+    // capacity-managed device buffers
+    int64_t cap_n = 0;
+    uint64_t* keys[2] = {nullptr, nullptr};
+    uint32_t* vals[2] = {nullptr, nullptr};
+    int sorted_buf = 0;       // which of keys/vals holds the sorted result
+    uint32_t* hist = nullptr; size_t hist_cap = 0;
+    float4* nodes = nullptr;
+    int32_t* parent = nullptr;     // [2n]: parent of leaf i at [i], of internal j at [n+j]
+    int32_t* visit = nullptr;      // [n] refit arrival counters
+    float4* geom = nullptr;
+    float4* shc = nullptr;
+    float4* aux = nullptr;
+    int32_t* perm = nullptr;       // sorted position -> caller index
+    float4* leafbox = nullptr;     // [2n] leaf boxes in sorted order (lo, hi)
+    unsigned int* bounds = nullptr;// [8] ordered-int min/max of the means
+    float* root = nullptr;         // [8] scene box
+    float4* grad = nullptr;        // [16n] backward accumulators (packed order)
+    int64_t grad_cap = 0;
+    // render
+    rgx_camera* cams = nullptr; int cams_cap = 0;
+    unsigned int* queue = nullptr; // [4] persistent work counters
+    unsigned int* status = nullptr;
+    unsigned long long* counters = nullptr; // [8]
+    char last_error[256] = {0};
+};
+
+// ordered mapping float <-> uint so that atomicMin/Max on uint orders floats
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// ---------------------------------------------------------------- SH
+// Real spherical harmonics up to degree 3 as polynomials in the unit
+// direction (x, y, z), Condon-Shortley phase, index k = l^2 + l + m.
+// Constants are K_l^m-normalisation values written out:
+//   1/(2 sqrt(pi)); sqrt(3/(4pi)); sqrt(15/(4pi)), sqrt(5/(16pi)), sqrt(15/(16pi));
+//   sqrt(35/(32pi)), sqrt(105/(4pi)), sqrt(21/(32pi)), sqrt(7/(16pi)), sqrt(105/(16pi)).
+__device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16]) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[0] = 0.28209479177387814f;
+    Y[1] = -0.48860251190291992f * y;
+    Y[2] = 0.48860251190291992f * z;
+    Y[3] = -0.48860251190291992f * x;
+    Y[4] = 1.0925484305920792f * x * y;
+    Y[5] = -1.0925484305920792f * y * z;
+    Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);
+    Y[7] = -1.0925484305920792f * x * z;
+    Y[8] = 0.54627421529603959f * (xx - yy);
+    Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
+    Y[10] = 2.8906114426405538f * x * y * z;
+    Y[11] = -0.45704579946446572f * y * (5.0f * zz - 1.0f);
+    Y[12] = 0.37317633259011540f * z * (5.0f * zz - 3.0f);
+    Y[13] = -0.45704579946446572f * x * (5.0f * zz - 1.0f);
+    Y[14] = 1.4453057213202769f * z * (xx - yy);
+    Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+}
+
+// ---------------------------------------------------------------- host helpers
+static inline rgx_status set_err(rgx_scene* s, rgx_status st, const char* msg) {
+    extern char g_rgx_last_error[256];
+    if (s) { strncpy(s->last_error, msg, sizeof(s->last_error) - 1); }
+    strncpy(g_rgx_last_error, msg, 255);
+    return st;
+}
+
+#define RGX_CUDA(s, call)                                                         \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            char m_[256];                                                         \
+            snprintf(m_, sizeof m_, "%s: %s", #call, cudaGetErrorString(e_));     \
+            return set_err((s), RGX_ERR_CUDA, m_);                                \
+        }                                                                         \
+    } while (0)
+
+// internal entry points shared between translation units
+rgx_status rgx_internal_reserve(rgx_scene* s, int64_t n);

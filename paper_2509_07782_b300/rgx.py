@@ -1,0 +1,267 @@
+"""ctypes binding of librgx (see include/rgx.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+If ``librgx.so`` is missing or cannot be loaded, importing the functions
+raises -- there is no CPU or PyTorch fallback.
+
+Module-level functions carry the C names (``rgx_build_bvh``,
+``rgx_render_forward``, ``rgx_render_backward`` ...) and take torch CUDA
+tensors; ``Scene`` and ``Cameras`` are small owners of the opaque handle and
+of the pinned camera array.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librgx.so")
+
+RGX_OK = 0
+RGX_ERR_INVALID_ARG = 1
+RGX_ERR_CUDA = 2
+RGX_ERR_WORKSPACE = 3
+RGX_ERR_STACK_OVERFLOW = 8
+RGX_ERR_ITER_LIMIT = 16
+RGX_ERR_BAD_PARAMS = 32
+RGX_ERR_REPLAY = 64
+RGX_ERR_NOT_BUILT = 128
+
+RGX_SKIP, RGX_ADAPTIVE, RGX_MORTON, RGX_ZTILES, RGX_MORTON63 = 1, 2, 4, 8, 16
+
+EXPORTS = ["rgx_scene_create", "rgx_scene_destroy", "rgx_build_bvh", "rgx_render_forward",
+           "rgx_render_forward_sched", "rgx_render_backward", "rgx_sync_status", "rgx_fwd_state_bytes",
+           "rgx_last_error", "rgx_get_bvh", "rgx_get_counters"]
+
+
+class RgxCamera(C.Structure):
+    _fields_ = [("c2w", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32),
+                ("t_near", C.c_float), ("t_far", C.c_float)]
+
+
+class RgxOpts(C.Structure):
+    _fields_ = [("flags", C.c_int32), ("dt", C.c_float), ("dt_min", C.c_float), ("dt_max", C.c_float),
+                ("beta", C.c_float), ("n_s", C.c_int32), ("t_eps", C.c_float), ("sigma_eps", C.c_float),
+                ("bg", C.c_float * 3), ("tile_w", C.c_int32), ("tile_h", C.c_int32),
+                ("hit_cap", C.c_int32), ("max_segments", C.c_int32)]
+
+
+class RgxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rgx error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> C.CDLL:
+    """Load librgx.so (raises if it is missing: no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"librgx.so not built at {LIB_PATH}; run python -m paper_2509_07782_b300.build_lib")
+            l = C.CDLL(LIB_PATH)
+            vp, fp, i64 = C.c_void_p, C.c_void_p, C.c_int64
+            l.rgx_scene_create.argtypes = [C.POINTER(vp), C.c_int32]
+            l.rgx_scene_destroy.argtypes = [vp]
+            l.rgx_build_bvh.argtypes = [vp, i64, C.c_int32, fp, fp, fp, fp, fp, C.POINTER(RgxOpts), vp]
+            l.rgx_render_forward.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), fp, vp, vp]
+            l.rgx_render_forward_sched.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), fp, vp,
+                                                   fp, C.c_int32, vp, vp]
+            l.rgx_render_backward.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), vp, fp,
+                                              fp, fp, fp, fp, fp, vp]
+            l.rgx_sync_status.argtypes = [vp, vp]
+            l.rgx_fwd_state_bytes.restype = C.c_size_t
+            l.rgx_fwd_state_bytes.argtypes = []
+            l.rgx_last_error.restype = C.c_char_p
+            l.rgx_last_error.argtypes = [vp]
+            l.rgx_get_bvh.argtypes = [vp, vp, vp, vp, vp, vp]
+            l.rgx_get_counters.argtypes = [vp, C.POINTER(C.c_uint64), vp]
+            for name in EXPORTS:
+                f = getattr(l, name)
+                if name not in ("rgx_fwd_state_bytes", "rgx_last_error"):
+                    f.restype = C.c_int32
+            _lib = l
+    return _lib
+
+
+def _check(code, handle=None):
+    if code != RGX_OK:
+        msg = lib().rgx_last_error(handle).decode(errors="replace")
+        raise RgxError(code, msg)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------ options
+def make_opts(o) -> RgxOpts:
+    """Convert a ``synth.Options``-like object into the C option struct."""
+    x = RgxOpts()
+    x.flags = ((RGX_SKIP if o.skip else 0) | (RGX_ADAPTIVE if o.adaptive else 0) |
+               (RGX_MORTON if o.morton else 0) | (RGX_ZTILES if o.ztiles else 0) |
+               (RGX_MORTON63 if o.morton63 else 0))
+    x.dt, x.dt_min, x.dt_max, x.beta = o.dt, o.dt_min, o.dt_max, o.beta
+    x.n_s, x.t_eps, x.sigma_eps = int(o.n_s), o.t_eps, o.sigma_eps
+    for i in range(3):
+        x.bg[i] = float(o.bg[i])
+    x.tile_w, x.tile_h, x.hit_cap, x.max_segments = int(o.tile_w), int(o.tile_h), int(o.hit_cap), int(o.max_segments)
+    return x
+
+
+class Cameras:
+    """Pinned host array of rgx_camera structs plus per-camera ray offsets."""
+
+    def __init__(self, cams):
+        self.cams = list(cams)
+        n = len(self.cams)
+        nbytes = C.sizeof(RgxCamera) * n
+        self._buf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=torch.cuda.is_available())
+        arr = (RgxCamera * n).from_address(self._buf.data_ptr())
+        for i, c in enumerate(self.cams):
+            m = np.asarray(c.c2w, dtype=np.float32).reshape(12)
+            for k in range(12):
+                arr[i].c2w[k] = float(m[k])
+            arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = c.fx, c.fy, c.cx, c.cy
+            arr[i].width, arr[i].height = int(c.width), int(c.height)
+            arr[i].t_near, arr[i].t_far = c.t_near, c.t_far
+        self.ptr = C.cast(C.c_void_p(self._buf.data_ptr()), C.POINTER(RgxCamera))
+        self.count = n
+        self.rays_per_cam = [c.width * c.height for c in self.cams]
+        self.offsets = np.concatenate([[0], np.cumsum(self.rays_per_cam)]).astype(np.int64)
+        self.n_rays = int(self.offsets[-1])
+
+
+# ------------------------------------------------------------------ C names
+def rgx_scene_create(device: int = 0):
+    h = C.c_void_p()
+    _check(lib().rgx_scene_create(C.byref(h), int(device)))
+    return h
+
+
+def rgx_scene_destroy(h):
+    lib().rgx_scene_destroy(h)
+
+
+def rgx_build_bvh(h, means, scales, quats, densities, sh, sh_degree, opts, stream=None):
+    n = int(means.shape[0])
+    _check(lib().rgx_build_bvh(h, n, int(sh_degree), _ptr(means), _ptr(scales), _ptr(quats), _ptr(densities),
+                               _ptr(sh), C.byref(opts), _stream(stream)), h)
+
+
+def rgx_render_forward(h, cams: Cameras, opts, rgba, state=None, stream=None):
+    _check(lib().rgx_render_forward(h, cams.ptr, cams.count, C.byref(opts), _ptr(rgba), _ptr(state),
+                                    _stream(stream)), h)
+
+
+def rgx_render_forward_sched(h, cams: Cameras, opts, rgba, state, sched, sched_n, stream=None):
+    _check(lib().rgx_render_forward_sched(h, cams.ptr, cams.count, C.byref(opts), _ptr(rgba), _ptr(state),
+                                          _ptr(sched), int(sched.shape[1]), _ptr(sched_n), _stream(stream)), h)
+
+
+def rgx_render_backward(h, cams: Cameras, opts, state, d_rgba, d_means, d_scales, d_quats, d_densities, d_sh,
+                        stream=None):
+    _check(lib().rgx_render_backward(h, cams.ptr, cams.count, C.byref(opts), _ptr(state), _ptr(d_rgba),
+                                     _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_densities), _ptr(d_sh),
+                                     _stream(stream)), h)
+
+
+def rgx_sync_status(h, stream=None) -> int:
+    return int(lib().rgx_sync_status(h, _stream(stream)))
+
+
+def rgx_fwd_state_bytes() -> int:
+    return int(lib().rgx_fwd_state_bytes())
+
+
+def rgx_get_bvh(h, n, stream=None):
+    dev = torch.device("cuda", torch.cuda.current_device())
+    codes = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    nodes = torch.empty(max(n - 1, 1), 16, dtype=torch.float32, device=dev)
+    root = torch.empty(6, dtype=torch.float32, device=dev)
+    _check(lib().rgx_get_bvh(h, _ptr(codes), _ptr(perm), _ptr(nodes), _ptr(root), _stream(stream)), h)
+    return codes[:n], perm[:n], nodes, root
+
+
+def rgx_get_counters(h, stream=None):
+    out = (C.c_uint64 * 8)()
+    _check(lib().rgx_get_counters(h, out, _stream(stream)), h)
+    keys = ["rays", "segments", "hits", "evals", "node_visits", "closest_hit", "skipped", "spare"]
+    return dict(zip(keys, [int(v) for v in out]))
+
+
+# ------------------------------------------------------------------ convenience
+class Scene:
+    """Owner of one rgx_scene handle on the current CUDA device."""
+
+    def __init__(self, device: int | None = None):
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.h = rgx_scene_create(self.device)
+        self.n = 0
+        self._keep = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                rgx_scene_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def build(self, means, scales, quats, densities, sh, opts, sh_degree: int = 3, stream=None):
+        self.n = int(means.shape[0])
+        rgx_build_bvh(self.h, means, scales, quats, densities, sh, sh_degree, opts, stream)
+
+    def forward(self, cams: Cameras, opts, want_state: bool = True, stream=None, sched_cap: int = 0):
+        dev = torch.device("cuda", self.device)
+        rgba = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
+        state = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev) if want_state else None
+        self._keep = cams
+        if sched_cap > 0:
+            sched = torch.zeros(cams.n_rays, sched_cap, 2, dtype=torch.float32, device=dev)
+            sched_n = torch.zeros(cams.n_rays, dtype=torch.int32, device=dev)
+            rgx_render_forward_sched(self.h, cams, opts, rgba, state, sched, sched_n, stream)
+            return rgba, state, sched, sched_n
+        rgx_render_forward(self.h, cams, opts, rgba, state, stream)
+        return rgba, state
+
+    def backward(self, cams: Cameras, opts, state, d_rgba, grads, stream=None):
+        self._keep = cams
+        rgx_render_backward(self.h, cams, opts, state, d_rgba, *grads, stream=stream)
+
+    def status(self, stream=None) -> int:
+        return rgx_sync_status(self.h, stream)
+
+    def bvh(self, stream=None):
+        return rgx_get_bvh(self.h, self.n, stream)
+
+    def counters(self, stream=None):
+        return rgx_get_counters(self.h, stream)
+
+
+def scene_tensors(scene, device="cuda"):
+    """Upload a ``synth.Scene`` as contiguous float32 CUDA tensors."""
+    def t(a):
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=device).contiguous()
+    nk = (scene.sh_degree + 1) ** 2
+    return (t(scene.means).reshape(-1, 3), t(scene.scales).reshape(-1, 3), t(scene.quats).reshape(-1, 4),
+            t(scene.densities).reshape(-1), t(scene.sh).reshape(-1, nk, 3))

@@ -1,0 +1,95 @@
+"""Forward parity of the CUDA march with the FP64 oracle (max-abs 1e-4 on RGB
+and opacity), through the C-ABI.
+
+* plain 2k / 64x64 (uniform step, no skipping): the full frame;
+* the same scene with every speed option (skip, adaptive, Z-order, tiles):
+  full frame at 64x64 and a ragged 37x23 view;
+* torus 100k at 800x800, in the configuration the benchmark times: 4,096
+  seeded pixels;
+* outdoor 3M (63-bit codes), batch 1M (8 uneven views, one launch) and
+  sweep 6M (64 views, one launch): seeded pixel samples at full size.
+In adaptive mode a pixel may exceed the tolerance only when the GPU took a
+segment decision that differs from the FP64 one by rounding: the oracle
+replaying the GPU's recorded schedule must then match, and such pixels must
+be rare.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_07782_b300 import synth
+from helpers import TOL_RGBA, compare_rgba, gpu_render
+
+pytestmark = pytest.mark.gpu
+
+
+def test_plain_2k_full_frame():
+    w = synth.workload("plain_2k")
+    r = gpu_render(w.scene, w.cameras, w.options)
+    assert r["status"] == 0
+    err, ndiv = compare_rgba(r["rgba"], w.cameras[0], w.scene, w.options)
+    assert err <= TOL_RGBA and ndiv == 0
+    assert r["rgba"][:, 3].max() > 0.9
+
+
+@pytest.mark.parametrize("res", [(64, 64), (37, 23)])
+def test_fast_options_full_frame(res):
+    w = synth.workload("plain_2k")
+    cam = w.cameras[0]
+    cam = synth.rescale_camera(cam, res[1] / cam.height)
+    cam = synth.Camera(cam.c2w, cam.fx, cam.fy, res[0] / 2, res[1] / 2, res[0], res[1])
+    o = synth.fast_options(dt=0.01)
+    r = gpu_render(w.scene, [cam], o, sched_cap=64)
+    assert r["status"] == 0
+    err, ndiv = compare_rgba(r["rgba"], cam, w.scene, o, gpu_sched=r["sched"], gpu_sched_n=r["sched_n"],
+                             max_divergent_frac=0.01)
+    assert err <= TOL_RGBA
+
+
+def test_uniform_skip_full_frame():
+    w = synth.workload("plain_2k")
+    o = synth.Options(skip=True, morton=True, ztiles=True, dt=0.01, n_s=16)
+    r = gpu_render(w.scene, w.cameras, o)
+    assert r["status"] == 0
+    err, _ = compare_rgba(r["rgba"], w.cameras[0], w.scene, o)
+    assert err <= TOL_RGBA
+
+
+def test_torus_100k_bench_configuration_sampled():
+    w = synth.workload("torus_100k")
+    cam = w.cameras[0]
+    r = gpu_render(w.scene, w.cameras, w.options, sched_cap=64)
+    assert r["status"] == 0
+    pix = synth.pixel_subset(cam, 4096, seed=7)
+    err, ndiv = compare_rgba(r["rgba"], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"],
+                             gpu_sched_n=r["sched_n"], max_divergent_frac=0.005)
+    assert err <= TOL_RGBA
+    assert (r["rgba"][:, 3] > 0.5).mean() > 0.05  # the object is in view
+
+
+def test_outdoor_3m_sampled():
+    w = synth.workload("outdoor_3m")
+    cam = w.cameras[0]
+    r = gpu_render(w.scene, w.cameras, w.options, sched_cap=96)
+    assert r["status"] == 0
+    pix = synth.pixel_subset(cam, 256, seed=8)
+    params = oracle.Params(w.scene)
+    err, ndiv = compare_rgba(r["rgba"], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"],
+                             gpu_sched_n=r["sched_n"], max_divergent_frac=0.02, params=params)
+    assert err <= TOL_RGBA
+
+
+@pytest.mark.parametrize("name,per_cam,ncam_checked", [("batch_1m", 48, 8), ("sweep_6m", 24, 4)])
+def test_batched_views_sampled(name, per_cam, ncam_checked):
+    w = synth.workload(name)
+    r = gpu_render(w.scene, w.cameras, w.options, sched_cap=48)
+    assert r["status"] == 0
+    offs = np.concatenate([[0], np.cumsum([c.n_rays for c in w.cameras])])
+    params = oracle.Params(w.scene)
+    for ci in range(0, len(w.cameras), max(1, len(w.cameras) // ncam_checked))[:ncam_checked]:
+        cam = w.cameras[ci]
+        pix = synth.pixel_subset(cam, per_cam, seed=100 + ci)
+        sl = slice(offs[ci], offs[ci + 1])
+        err, _ = compare_rgba(r["rgba"][sl], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"][sl],
+                              gpu_sched_n=r["sched_n"][sl], max_divergent_frac=0.05, params=params)
+        assert err <= TOL_RGBA
