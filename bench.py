@@ -1,0 +1,415 @@
+#!/usr/bin/env python3
+"""Benchmark of the differentiable Gaussian ray-marching step on B300.
+
+One step = the whole hot path on one batch: rgx_build_bvh (bounds, Morton
+codes, radix sort, radix tree, refit, packing) + rgx_render_forward (skip +
+adaptive step + Z-order storage + Z-order ray tiles) + rgx_render_backward
+(replayed adjoint + per-Gaussian finalisation), on the torus workload:
+100,000 seeded Gaussians, one 800x800 view on a radius-4 orbit.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  ``value`` is whole-job Mrays/s of the step
+with inputs resident in HBM, timed with CUDA events per step on the launching
+stream, L2 flushed (256 MiB write) between steps outside the events.
+``e2e`` repeats the step through the same C-ABI with host (pinned) buffers,
+host<->device copies inside the timed region.  ``--impl reference`` times the
+FP64 CPU oracle on the host cores on a bounded pixel sample instead.
+Multi-GPU (torchrun): each rank renders its own seeded camera of the same
+scene (weak scaling); ranks share nothing on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "torus_100k"
+METRIC = "Mrays/s render & fwd+bwd ms/iter vs plain marcher at ≤1e-4 err; % HBM peak"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="rgx", choices=["rgx", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    for path in (os.path.join(ROOT, "MEASURED_PEAKS.json"),):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+def launches_per_step(opts) -> int:
+    passes = 8 if opts.morton63 else 4
+    build = 2 + 3 * passes + 1 + 2       # bounds, morton, sort passes, pack, karras + refit
+    return build + 1 + 2                  # forward march; backward march + finalize
+
+
+def algorithmic_counts(counters_fwd, counters_bwd):
+    return counters_fwd, counters_bwd
+
+
+def alu_model(evals, hits, segs, rays, ns, backward: bool):
+    """FP32 FLOP-equivalents of the algorithmic work of one march launch.
+
+    Per (sample, Gaussian) evaluation: sample offset (FMA), quadratic form
+    (MUL + FMA), exponent (FMA), 1 ex2 on the SFU, density add, 3 colour FMA
+    -> 14 FP32 FLOPs + 1 ex2; the adjoint replays that and adds the
+    dL/dg product (3 FMA + mul), 3 moment FMA (+2 mul) and 3 colour-gradient FMA
+    -> +22 FLOPs.  Per (ray, segment, Gaussian) hit: chord solve (~60 FLOPs),
+    SH colour (48 FMA = 96 FLOPs); the adjoint doubles these and adds the
+    moment expansion (~60) and 59 atomically added floats.  One ex2 is
+    counted as 16 FLOP-equivalents (128 FP32 lanes x 2 vs 16 SFU results per
+    SM per clock), so the FP32 pipe peak is the single denominator.
+    """
+    per_eval = 14 + 16
+    per_hit = 60 + 96
+    if backward:
+        per_eval = 2 * per_eval + 22
+        per_hit = 2 * per_hit + 60
+    return evals * per_eval + hits * per_hit
+
+
+def run_rgx(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_07782_b300 import rgx, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.workload(WORKLOAD)
+    if rank > 0:  # weak scaling: every rank renders its own seeded camera of the same scene
+        cam0 = w.cameras[0]
+        rng = np.random.Generator(np.random.PCG64(5000 + rank))
+        w.cameras = [synth.orbit_camera(rng, 4.0, cam0.width, cam0.height)]
+    opts = rgx.make_opts(w.options)
+    cams = rgx.Cameras(w.cameras)
+    R = cams.n_rays
+    t = rgx.scene_tensors(w.scene, device=dev)
+    sc = rgx.Scene(local)
+    stream = torch.cuda.current_stream()
+    upstream = torch.randn(R, 4, device=dev, generator=torch.Generator(device=dev).manual_seed(1 + rank))
+    grads = [torch.zeros_like(x) for x in t]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        sc.build(*t, opts)
+        if ev is not None:
+            ev[1].record(stream)
+        rgba, state = sc.forward(cams, opts)
+        if ev is not None:
+            ev[2].record(stream)
+        for g in grads:
+            g.zero_()
+        sc.backward(cams, opts, state, upstream, grads)
+        if ev is not None:
+            ev[3].record(stream)
+        return rgba
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st = sc.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after warm-up")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    barrier()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        step(evs[i])
+        flush.fill_(float(i))  # L2 flush between steps, outside the events
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    fwd_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    total_ms = float(sum(step_ms))
+    st = sc.status()
+
+    # work counters of one forward and one backward (separate, untimed calls)
+    rgba, state = sc.forward(cams, opts)
+    cf = sc.counters()
+    for g in grads:
+        g.zero_()
+    sc.backward(cams, opts, state, upstream, grads)
+    cb = sc.counters()
+    torch.cuda.synchronize()
+
+    # e2e through the C-ABI with host buffers: H2D params + upstream, D2H grads + rgba
+    host_in = [x.cpu().pin_memory() for x in t] + [upstream.cpu().pin_memory()]
+    host_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in t] + \
+               [torch.empty(R, 4, dtype=torch.float32, pin_memory=True)]
+    dev_in = [torch.empty_like(x) for x in t] + [torch.empty_like(upstream)]
+    h2d = sum(x.numel() * x.element_size() for x in host_in)
+    d2h = sum(x.numel() * x.element_size() for x in host_out)
+
+    def e2e_step():
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+        sc.build(*dev_in[:5], opts)
+        rgba_, state_ = sc.forward(cams, opts)
+        gl = [torch.zeros_like(x) for x in dev_in[:5]]
+        sc.backward(cams, opts, state_, dev_in[5], gl)
+        for h, d in zip(host_out, gl + [rgba_]):
+            h.copy_(d, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+
+    # the plain single-view marcher on the same GPU (uniform step = dt_min, no skip,
+    # caller-order storage, scanline rays): forward and forward+adjoint
+    plain = None
+    if not args.no_plain:
+        po = synth.Options(dt=w.options.dt_min, n_s=w.options.n_s, sigma_eps=w.options.sigma_eps,
+                           hit_cap=w.options.hit_cap)
+        popts = rgx.make_opts(po)
+        sp = rgx.Scene(local)
+        for _ in range(2):
+            sp.build(*t, popts)
+            _, pst = sp.forward(cams, popts)
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        fm, fb = [], []
+        for i in range(3):
+            sp.build(*t, popts)
+            a.record(stream)
+            _, pst = sp.forward(cams, popts)
+            b.record(stream)
+            gl = [torch.zeros_like(x) for x in t]
+            sp.backward(cams, popts, pst, upstream, gl)
+            c.record(stream)
+            torch.cuda.synchronize()
+            fm.append(a.elapsed_time(b))
+            fb.append(b.elapsed_time(c))
+            flush.fill_(0.0)
+        plain = {"fwd_ms": statistics.median(fm), "bwd_ms": statistics.median(fb),
+                 "render_mrays_s": R / statistics.median(fm) / 1e3,
+                 "options": "uniform dt=0.005, N_S=16, no skip, caller order, scanline rays"}
+        if sp.status() != 0:
+            plain["status"] = "device status nonzero"
+
+    # max over ranks
+    vals = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    total_ms, e2e_ms = float(vals[0]), float(vals[1])
+    ms_per_step = total_ms / args.steps
+    value = world * R * args.steps / (total_ms / 1e3) / 1e6
+    return dict(R=R, ms_per_step=ms_per_step, value=value, build_ms=statistics.median(build_ms),
+                fwd_ms=statistics.median(fwd_ms), bwd_ms=statistics.median(bwd_ms), wall_s=wall,
+                e2e=dict(value=world * R / (e2e_ms / 1e3) / 1e6, unit="Mrays/s", h2d_bytes_per_step=h2d,
+                         d2h_bytes_per_step=d2h, ms_per_step=e2e_ms),
+                counters_fwd=cf, counters_bwd=cb, clocks=clocks, status=st, plain=plain, opts=w.options,
+                n=w.scene.n, steps_launches=launches_per_step(w.options) * args.steps)
+
+
+def cpu_baseline(max_seconds=12.0, npix_start=256):
+    """FP64 oracle (as it stands) on the host cores: forward + adjoint on a
+    seeded pixel sample of the same view, grown until ~max_seconds."""
+    import oracle
+    from paper_2509_07782_b300 import synth
+    w = synth.workload(WORKLOAD)
+    cam = w.cameras[0]
+    P = oracle.Params(w.scene)
+    cores = os.cpu_count() or 1
+    npix = npix_start
+    while True:
+        pix = synth.pixel_subset(cam, npix, seed=3)
+        W = np.random.default_rng(4).normal(size=(len(pix), 4))
+        t0 = time.perf_counter()
+        oracle.render(w.scene, cam, w.options, pix=pix, params=P, nthreads=cores)
+        oracle.backward(w.scene, cam, w.options, W, pix=pix, params=P, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if dt > max_seconds / 4 or npix >= cam.n_rays:
+            break
+        npix = min(cam.n_rays, npix * 4)
+    return {"value": len(pix) / dt / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(pix)} seeded pixels of the 800x800 view, forward + adjoint, {dt:.2f} s"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        from paper_2509_07782_b300 import synth
+        w = synth.workload(WORKLOAD)
+        cam = w.cameras[0]
+        P = oracle.Params(w.scene)
+        cores = os.cpu_count() or 1
+        pix = synth.pixel_subset(cam, 2048, seed=3)
+        W = np.random.default_rng(4).normal(size=(len(pix), 4))
+        for _ in range(max(args.warmup, 0)):
+            oracle.render(w.scene, cam, w.options, pix=pix[:64], params=P, nthreads=cores)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            oracle.render(w.scene, cam, w.options, pix=pix, params=P, nthreads=cores)
+            oracle.backward(w.scene, cam, w.options, W, pix=pix, params=P, nthreads=cores)
+            times.append(time.perf_counter() - t0)
+        tot = sum(times)
+        v = len(pix) * args.steps / tot / 1e6
+        out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s", "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": f"{WORKLOAD}: 100k Gaussians, 800x800 view, "
+                                               "forward + adjoint, skip + adaptive + Z-order",
+                                               "sample": f"{len(pix)} seeded pixels per step"},
+               "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{len(pix)} seeded pixels per step, forward + adjoint"},
+               "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    r = run_rgx(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    peaks, src = load_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2
+    cb, cf = r["counters_bwd"], r["counters_fwd"]
+    ns = r["opts"].n_s
+    flops_b = alu_model(cb["evals"], cb["hits"], cb["segments"], cb["rays"], ns, True)
+    flops_f = alu_model(cf["evals"], cf["hits"], cf["segments"], cf["rays"], ns, False)
+    # dominant kernel: the backward march (its call also zeroes the accumulators and finalises)
+    bwd_s = r["bwd_ms"] / 1e3
+    fwd_s = r["fwd_ms"] / 1e3
+    dominant_is_bwd = r["bwd_ms"] >= r["fwd_ms"]
+    achieved = (flops_b / bwd_s if dominant_is_bwd else flops_f / fwd_s) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_march<16,bwd>" if dominant_is_bwd else "k_march<16,fwd>",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": None,
+                "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived), HBM {src} "
+                               f"{peaks.get('hbm_gbs')} GB/s"}
+    out = {
+        "metric": METRIC, "value": r["value"], "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: {r['n']} Gaussians on a torus, one 800x800 view, BVH rebuild + "
+                               "forward + adjoint (skip + adaptive Eq.5 + Z-order + 8x4 Z-tiles, N_S=16)",
+                   "rays_per_step_per_gpu": r["R"], "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"{world} independent views, no data-path collective"},
+        "fwd_bwd_ms": r["fwd_ms"] + r["bwd_ms"], "build_ms": r["build_ms"], "fwd_ms": r["fwd_ms"],
+        "bwd_ms": r["bwd_ms"], "render_mrays_s": r["R"] / r["fwd_ms"] / 1e3,
+        "plain_marcher": r["plain"],
+        "speedup_vs_plain": {"render": (r["plain"]["fwd_ms"] / r["fwd_ms"]) if r["plain"] else None,
+                             "fwd_bwd": ((r["plain"]["fwd_ms"] + r["plain"]["bwd_ms"]) / (r["fwd_ms"] + r["bwd_ms"]))
+                             if r["plain"] else None},
+        "roofline": roofline,
+        "work": {"fwd": cf, "bwd": cb},
+        "e2e": r["e2e"], "gpu_launches": r["steps_launches"], "clocks": r["clocks"],
+        "device_status": r["status"],
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

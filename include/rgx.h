@@ -83,7 +83,7 @@ typedef struct {
     float sigma_eps;             /* truncation density: support is sigma(x) >= sigma_eps */
     float bg[3];                 /* background colour, added as T_final * bg */
     int32_t tile_w, tile_h;      /* ray tile, tile_w * tile_h == 32 (ZTILES only) */
-    int32_t hit_cap;             /* hit-list chunk per ray (8..256); never drops hits */
+    int32_t hit_cap;             /* chord-list capacity per ray (32..512); never drops hits */
     int32_t max_segments;        /* loop bound per ray; 0 = derived from the ray length */
 } rgx_opts;
 
@@ -154,6 +154,26 @@ rgx_status rgx_render_backward(rgx_scene* scene, const rgx_camera* cams, int32_t
                                float* d_means, float* d_scales, float* d_quats,
                                float* d_densities, float* d_sh, void* stream);
 
+/*
+ * Autotuner for the open knobs of Algorithm 1 -- samples per segment N_S, the
+ * capacity of the hit-primitive buffer H_b (hit_cap) -- and of the 2D ray
+ * tiles of Sec. 3.3 (tile_w x tile_h, when RGX_ZTILES is set).  Each candidate
+ * (4 tile shapes x hit_cap in {64,128,256,512} x N_S in {8,16,32} when
+ * tune_ns != 0, else base->n_s) is run once to warm up and twice timed with
+ * CUDA events on `stream`, forward only or forward + adjoint
+ * (with_backward != 0), on the caller's scene and cameras; the fastest
+ * options are written to *best (other fields copied from *base) and the time
+ * in ms to *best_ms (may be NULL).  Synchronises the stream.  rgba,
+ * fwd_state, d_rgba and the five gradient arrays are caller-owned scratch
+ * buffers laid out as for rgx_render_forward / rgx_render_backward; their
+ * contents are undefined afterwards.  Note that N_S changes results in
+ * adaptive mode (Eq. 5 scales with N_S), so tune_ns = 0 keeps results fixed.
+ */
+rgx_status rgx_autotune(rgx_scene* scene, const rgx_camera* cams, int32_t ncam, const rgx_opts* base,
+                        int32_t tune_ns, int32_t with_backward, float* rgba, void* fwd_state,
+                        const float* d_rgba, float* d_means, float* d_scales, float* d_quats,
+                        float* d_densities, float* d_sh, rgx_opts* best, float* best_ms, void* stream);
+
 /* Synchronise `stream`, return the device status word (RGX_ERR_* bits, 0 if
  * clean) and clear it. */
 rgx_status rgx_sync_status(rgx_scene* scene, void* stream);
@@ -181,7 +201,8 @@ rgx_status rgx_get_bvh(rgx_scene* scene, uint64_t* codes, int32_t* perm, float* 
  * Work counters of the last forward or backward call (HOST output, 8 x
  * uint64; synchronises the stream): [0] rays, [1] evaluated segments,
  * [2] (ray, segment, Gaussian) hits, [3] (sample, Gaussian) evaluations,
- * [4] BVH node visits, [5] ClosestHit queries, [6] skipped segments, [7] 0.
+ * [4] BVH node visits, [5] ClosestHit queries, [6] skipped segments,
+ * [7] chord windows collected.
  */
 rgx_status rgx_get_counters(rgx_scene* scene, uint64_t* out8, void* stream);
 

@@ -58,6 +58,11 @@ struct rgx_scene {
     unsigned int* queue = nullptr; // [4] persistent work counters
     unsigned int* status = nullptr;
     unsigned long long* counters = nullptr; // [8]
+    // launch-configuration cache: (kernel, dynamic smem) -> resident blocks/SM,
+    // so that calls inside a CUDA-graph capture make no attribute queries
+    struct LaunchCfg { const void* k; size_t smem; int occ; };
+    LaunchCfg cfg[32];
+    int ncfg = 0;
     char last_error[256] = {0};
 };
 

@@ -1,38 +1,46 @@
 // march.cu -- forward volume ray marching and its adjoint (Algorithm 1, Eq. 1-5).
 //
-// One thread marches one ray.  A warp owns a 32-ray tile popped from a
-// persistent work counter shared by every camera of the launch (2D Z-order
-// tiles with RGX_ZTILES, 32 consecutive scanline pixels otherwise).  Per
-// segment [t_S, t_S + dS) the thread
-//   1. collects the BVH leaves whose boxes overlap the segment, in ascending
-//      leaf order, into its slice of shared memory (hit_cap entries; larger
-//      lists are processed in chunks by restarting the traversal after the last
-//      leaf taken, so no hit is ever dropped);
-//   2. for every collected Gaussian solves its exact ellipsoid chord; those
-//      whose chord overlaps the segment are the segment's hit set (Algorithm 1's
-//      BVHTraversal, with segments wholly inside an ellipsoid included);
-//   3. adds each hit's density sigma~ exp(-q/2) (hard-truncated at Q_eps) and
-//      density-weighted SH colour to the N_S per-sample accumulators in
-//      registers (Eq. 1), hits outer / samples inner;
-//   4. composites the N_S samples front to back (Eq. 3).
-// An empty hit set advances by dS, or with RGX_SKIP jumps to ClosestHit (Eq. 4).
+// Warp-per-ray design.  A warp pops a 32-ray tile from a persistent work
+// counter shared by every camera of the launch (2D Z-order tiles with
+// RGX_ZTILES, 32 consecutive scanline pixels otherwise) and marches the tile's
+// rays one after another with all 32 lanes, so the control flow of a ray never
+// diverges across lanes.  For a ray the warp
+//   1. collects, by a cooperative BVH traversal (up to 32 nodes per step, a
+//      shared-memory stack), the exact ellipsoid chords [t_in, t_out] of every
+//      Gaussian overlapping a *window* [t_S, t_S + W) that spans one or more
+//      segments, together with the per-(ray, Gaussian) quadratic
+//      q(t) = q_min + a (t - t_c)^2 and SH colour c_l(d) -- once per window
+//      instead of once per segment.  W adapts to the list capacity (hit_cap);
+//      a single segment whose hits exceed it is processed in chunks, so no
+//      hit is ever dropped;
+//   2. takes, per segment [t_S, t_S + dS), the chords overlapping it: that is
+//      the segment's hit set of Algorithm 1 (BVHTraversal), including segments
+//      wholly inside an ellipsoid;
+//   3. evaluates lane-parallel over samples (lane = sample k; 32/N_S lane groups
+//      split the hits) sigma_k = sum_l sigma~_l exp(-q_l/2) (hard truncation at
+//      Q_eps) and S_k = sum_l g_l c_l (Eq. 1), then composites the N_S samples
+//      with a multiplicative warp scan for T_k (Eq. 3);
+//   4. an empty hit set advances by dS, or with RGX_SKIP jumps to ClosestHit
+//      (Eq. 4): from the window's chords when they decide it, else by a
+//      cooperative nearest-hit traversal.
 //
-// The adjoint kernel replays exactly the same arithmetic (same hit order, same
-// explicitly rounded operations), so it reproduces T and the schedule bit for
-// bit without storing any sample.  Using the residual C_final - C_<=i it
-// forms dL/dsigma_i and dL/dc_i per sample, then per hit accumulates over the
-// samples three scalars (sum w, sum w u, sum w u^2, w = dL/dg * g, u the
-// sample offset from the chord centre) and dL/dc_l; these give the local-frame
-// moments A0, V = sum w y, P = sum w y y^T that are atomically added per
-// Gaussian.  k_grad_finalize chains them to mu, s, q, sigma~ (and scatters SH
-// gradients) once per Gaussian.
+// The adjoint kernel replays exactly the same decisions and arithmetic, so it
+// reproduces T and the schedule bit for bit without storing any sample.  Per
+// segment it forms beta_k = dL/dsigma_k - gamma_k.c_k and gamma_k = dL/dc_k /
+// sigma_k from the residual C_final - C_<=k, then hit-parallel accumulates per
+// (ray, Gaussian) over all samples of the window sum w, sum w u, sum w u^2
+// (w = dL/dg g, u = t - t_c) and dL/dc_l; at the end of the window these give the
+// local-frame moments A0, V = sum w y, P = sum w y y^T that are added atomically
+// per Gaussian.  k_grad_finalize chains them to mu, s, q, sigma~ once per Gaussian.
 #include <stdio.h>
 #include "common.cuh"
 
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
-#define DONE 0xffffffffu
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
+#define WARPS (RGX_BLOCK / 32)
+#define STK 256                                     // per-warp traversal stack
+#define CANDS 64                                    // leaf candidates per traversal step
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -62,13 +70,52 @@ struct MarchParams {
 
 struct Ray {
     float ox, oy, oz, dx, dy, dz;
-    float ix, iy, iz;        // 1/d
+    float ix, iy, iz;  // 1/d
 };
 
 struct Counters {
-    unsigned segs, hits, evals, visits, chq, skips;
+    unsigned segs, hits, evals, visits, chq, skips, windows;
 };
 
+// ------------------------------------------------------------------ per-warp shared memory
+struct WS {
+    float4* q;      // [cap] (t_c, a, q_min, Q_eps)
+    float4* c;      // [cap] (log2 sigma~, c0, c1, c2)
+    float4* acc;    // [cap] (A0, A1, A2, dc0)     adjoint only
+    float2* acc2;   // [cap] (dc1, dc2)            adjoint only
+    float2* tio;    // [cap] (t_in, t_out)
+    float4* bg;     // [32]  (beta, gamma0..2)     adjoint only
+    uint32_t* pid;  // [cap] packed index
+    uint32_t* seg;  // [cap] entries of the current segment
+    uint32_t* stk;  // [STK] node refs
+    float* stkt;    // [STK] entry distance (nearest-hit traversal)
+    uint32_t* cand; // [CANDS]
+};
+
+__host__ __device__ inline size_t warp_bytes(int cap, bool bwd) {
+    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + CANDS * 4;
+    if (bwd) b += (size_t)cap * (16 + 8) + 32 * 16;
+    return (b + 15) & ~(size_t)15;
+}
+
+__device__ inline WS carve(char* base, int cap, bool bwd) {
+    WS w;
+    char* p = base;
+    w.q = (float4*)p; p += (size_t)cap * 16;
+    w.c = (float4*)p; p += (size_t)cap * 16;
+    if (bwd) { w.acc = (float4*)p; p += (size_t)cap * 16; w.bg = (float4*)p; p += 32 * 16; }
+    else { w.acc = nullptr; w.bg = nullptr; }
+    w.tio = (float2*)p; p += (size_t)cap * 8;
+    if (bwd) { w.acc2 = (float2*)p; p += (size_t)cap * 8; } else w.acc2 = nullptr;
+    w.stkt = (float*)p; p += (size_t)STK * 4;
+    w.pid = (uint32_t*)p; p += (size_t)cap * 4;
+    w.seg = (uint32_t*)p; p += (size_t)cap * 4;
+    w.stk = (uint32_t*)p; p += (size_t)STK * 4;
+    w.cand = (uint32_t*)p;
+    return w;
+}
+
+// ------------------------------------------------------------------ geometry
 // Slab test of box [lo, hi] against the ray over [ta, tb].  Empty boxes are
 // stored inverted (lo = +inf, hi = -inf) and always miss.
 __device__ __forceinline__ bool box_overlap(float4 lo, float4 hi, const Ray& r, float ta, float tb, float& tentry) {
@@ -83,17 +130,16 @@ __device__ __forceinline__ bool box_overlap(float4 lo, float4 hi, const Ray& r, 
 
 // Exact chord of the Q_eps ellipsoid of Gaussian p: q(t) = qmin + a (t - tc)^2.
 struct Chord {
-    float tc, a, qmin, Qe, L;      // L = log2 sigma~
+    float tc, a, qmin, Qe, L;
     float tin, tout;
     bool ok;
 };
 
-__device__ __forceinline__ Chord chord_of(const float4* __restrict__ geom, int64_t p, const Ray& r,
-                                          float4& g1, float4& g2, float4& g3, float4& g0) {
-    g0 = __ldg(&geom[4 * p + 0]);
-    g1 = __ldg(&geom[4 * p + 1]);
-    g2 = __ldg(&geom[4 * p + 2]);
-    g3 = __ldg(&geom[4 * p + 3]);
+__device__ __forceinline__ Chord chord_of(const float4* __restrict__ geom, int64_t p, const Ray& r) {
+    const float4 g0 = __ldg(&geom[4 * p + 0]);
+    const float4 g1 = __ldg(&geom[4 * p + 1]);
+    const float4 g2 = __ldg(&geom[4 * p + 2]);
+    const float4 g3 = __ldg(&geom[4 * p + 3]);
     Chord c;
     const float ex = r.ox - g0.x, ey = r.oy - g0.y, ez = r.oz - g0.z;
     const float y0x = g1.x * ex + g1.y * ey + g1.z * ez;
@@ -116,9 +162,13 @@ __device__ __forceinline__ Chord chord_of(const float4* __restrict__ geom, int64
     return c;
 }
 
-// Local-frame quantities the adjoint needs: y_c = y(tc) and yd = M d.
-__device__ __forceinline__ void local_frame(float4 g0, float4 g1, float4 g2, float4 g3, const Ray& r, float tc,
+// y_c = M (o + t_c d - mu) and yd = M d of Gaussian p.
+__device__ __forceinline__ void local_frame(const float4* __restrict__ geom, int64_t p, const Ray& r, float tc,
                                             float yc[3], float yd[3]) {
+    const float4 g0 = __ldg(&geom[4 * p + 0]);
+    const float4 g1 = __ldg(&geom[4 * p + 1]);
+    const float4 g2 = __ldg(&geom[4 * p + 2]);
+    const float4 g3 = __ldg(&geom[4 * p + 3]);
     const float ex = r.ox - g0.x, ey = r.oy - g0.y, ez = r.oz - g0.z;
     yd[0] = g1.x * r.dx + g1.y * r.dy + g1.z * r.dz;
     yd[1] = g2.x * r.dx + g2.y * r.dy + g2.z * r.dz;
@@ -128,110 +178,13 @@ __device__ __forceinline__ void local_frame(float4 g0, float4 g1, float4 g2, flo
     yc[2] = g3.x * ex + g3.y * ey + g3.z * ez + tc * yd[2];
 }
 
-// Left-first DFS over the radix tree collecting leaves >= cursor whose boxes
-// overlap [ta, tb].  Returns the number collected; cursor becomes the first
-// leaf not yet taken (DONE when the traversal finished).
-__device__ int collect(const MarchParams& P, const Ray& r, float ta, float tb, uint32_t* __restrict__ hl,
-                       int cap, uint32_t& cursor, uint32_t* __restrict__ stk, Counters& cnt) {
-    const uint32_t start = cursor;
-    int count = 0, sp = 0;
-    uint32_t ref = 0;  // root (internal node 0)
-    float te;
-    while (true) {
-        if (ref & LEAF_BIT) {
-            const uint32_t leaf = ref & ~LEAF_BIT;
-            if (count == cap) { cursor = leaf; return count; }
-            hl[count * RGX_BLOCK] = leaf;
-            count++;
-        } else {
-            cnt.visits++;
-            const float4* nd = P.nodes + 4 * (size_t)ref;
-            const float4 a0 = __ldg(nd), a1 = __ldg(nd + 1), a2 = __ldg(nd + 2), a3 = __ldg(nd + 3);
-            const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
-            const bool hl_ = (split >= start) && box_overlap(a0, a1, r, ta, tb, te);
-            const bool hr_ = (last >= start) && box_overlap(a2, a3, r, ta, tb, te);
-            const uint32_t rl = (first == split) ? (split | LEAF_BIT) : split;
-            const uint32_t rr = (split + 1 == last) ? ((split + 1) | LEAF_BIT) : (split + 1);
-            if (hl_ && hr_) {
-                if (sp < RGX_STACK) stk[sp++] = rr; else atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
-                ref = rl;
-                continue;
-            }
-            if (hl_) { ref = rl; continue; }
-            if (hr_) { ref = rr; continue; }
-        }
-        if (sp == 0) { cursor = DONE; return count; }
-        ref = stk[--sp];
-    }
-}
-
-// ClosestHit(ta) = min over Gaussians whose chord has t_out > ta and
-// t_in < tf of max(t_in, ta); tf if there is none (Algorithm 1, Eq. 4).
-// Nearest-first traversal pruned by the best value found so far.
-__device__ float closest_hit(const MarchParams& P, const Ray& r, float ta, float tf, uint32_t* __restrict__ stk,
-                             float* __restrict__ tstk, Counters& cnt) {
-    cnt.chq++;
-    float best = tf;
-    int sp = 0;
-    uint32_t ref = 0;
-    while (true) {
-        if (!(ref & LEAF_BIT)) {
-            cnt.visits++;
-            const float4* nd = P.nodes + 4 * (size_t)ref;
-            const float4 a0 = __ldg(nd), a1 = __ldg(nd + 1), a2 = __ldg(nd + 2), a3 = __ldg(nd + 3);
-            const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
-            float tl, tr;
-            bool hl_ = box_overlap(a0, a1, r, ta, best, tl);
-            bool hr_ = box_overlap(a2, a3, r, ta, best, tr);
-            uint32_t rl = (first == split) ? (split | LEAF_BIT) : split;
-            uint32_t rr = (split + 1 == last) ? ((split + 1) | LEAF_BIT) : (split + 1);
-            // leaves are resolved at once
-            for (int side = 0; side < 2; side++) {
-                const bool h = side ? hr_ : hl_;
-                const uint32_t rf = side ? rr : rl;
-                if (h && (rf & LEAF_BIT)) {
-                    const uint32_t leaf = rf & ~LEAF_BIT;
-                    const int64_t p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
-                    float4 g0, g1, g2, g3;
-                    const Chord c = chord_of(P.geom, p, r, g1, g2, g3, g0);
-                    if (c.ok && c.tout > ta && c.tin < tf) {
-                        const float t = fmaxf(c.tin, ta);
-                        if (t < best) best = t;
-                    }
-                    if (side) hr_ = false; else hl_ = false;
-                }
-            }
-            if (best <= ta) return ta;
-            if (hl_ && tl >= best) hl_ = false;
-            if (hr_ && tr >= best) hr_ = false;
-            if (hl_ && hr_) {
-                const bool lfirst = tl <= tr;
-                if (sp < RGX_STACK) { stk[sp] = lfirst ? rr : rl; tstk[sp] = lfirst ? tr : tl; sp++; }
-                else atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
-                ref = lfirst ? rl : rr;
-                continue;
-            }
-            if (hl_) { ref = rl; continue; }
-            if (hr_) { ref = rr; continue; }
-        }
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            if (tstk[sp] < best) { ref = stk[sp]; found = true; break; }
-        }
-        if (!found) return best;
-    }
-}
-
-// SH colour c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_k); `pre` keeps the argument.
-__device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_t p, const float Y[16], float c[3],
-                                          float pre[3]) {
+// SH colour c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_k).
+__device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_t p, const float Y[16], float c[3]) {
     const float4* s = shc + 12 * p;
     float r = 0.5f, g = 0.5f, b = 0.5f;
 #pragma unroll
     for (int j = 0; j < 12; j++) {
         const float4 v = __ldg(&s[j]);
-        // coefficient index 4j..4j+3 in (k, channel) order
         const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int e = 0; e < 4; e++) {
@@ -241,25 +194,232 @@ __device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_
             if (ch == 0) r += t; else if (ch == 1) g += t; else b += t;
         }
     }
-    pre[0] = r; pre[1] = g; pre[2] = b;
     c[0] = fmaxf(r, 0.0f); c[1] = fmaxf(g, 0.0f); c[2] = fmaxf(b, 0.0f);
 }
 
-// Per-sample evaluation of one hit over the N_S samples of a segment.
-template <int NS>
-__device__ __forceinline__ void eval_hit(const Chord& c, float u0, float dtk, const float col[3], float sig[NS],
-                                         float S[NS][3]) {
+__device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
-    for (int k = 0; k < NS; k++) {
-        const float u = __fmaf_rn((float)k, dtk, u0);
-        const float q = __fmaf_rn(__fmul_rn(c.a, u), u, c.qmin);
-        if (q <= c.Qe) {
-            const float g = exp2f(__fmaf_rn(q, NEG_HALF_LOG2E, c.L));
-            sig[k] = __fadd_rn(sig[k], g);
-            S[k][0] = __fmaf_rn(g, col[0], S[k][0]);
-            S[k][1] = __fmaf_rn(g, col[1], S[k][1]);
-            S[k][2] = __fmaf_rn(g, col[2], S[k][2]);
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULLMASK, v, o));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
+
+// ------------------------------------------------------------------ traversals
+struct NoChunk {
+    __device__ void operator()(int) const {}
+};
+
+// Collect into the list every Gaussian whose exact chord overlaps [ta, tb).
+// Returns 0 when complete, 1 when the list would overflow (window mode: the
+// caller shrinks the window), 2 on a traversal-stack overflow.  In chunked
+// mode a full list is handed to `on_full(m)` and reset instead.
+template <bool BWD, class OnFull>
+__device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, const float Y[16], float ta, float tb,
+                         int cap, int& nL, bool chunked, OnFull on_full, Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    if (lane == 0) W.stk[0] = 0u;
+    __syncwarp();
+    int sp = 1;
+    while (sp > 0) {
+        const int room = (STK - sp) / 2;
+        const int take = min(min(sp, 32), room);
+        if (take <= 0) {
+            if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
+            return 2;
         }
+        const int base = sp - take;
+        const uint32_t ref = lane < take ? W.stk[base + lane] : 0u;
+        __syncwarp();
+        sp = base;
+        bool hl_ = false, hr_ = false;
+        uint32_t rl = 0, rr = 0;
+        if (lane < take) {
+            cnt.visits++;
+            const float4* nd = P.nodes + 4 * (size_t)ref;
+            const float4 a0 = __ldg(nd), a1 = __ldg(nd + 1), a2 = __ldg(nd + 2), a3 = __ldg(nd + 3);
+            const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
+            float te;
+            hl_ = box_overlap(a0, a1, r, ta, tb, te);
+            hr_ = box_overlap(a2, a3, r, ta, tb, te);
+            rl = (first == split) ? (split | LEAF_BIT) : split;
+            rr = (split + 1 == last) ? ((split + 1) | LEAF_BIT) : (split + 1);
+        }
+        const bool pl = hl_ && !(rl & LEAF_BIT), pr = hr_ && !(rr & LEAF_BIT);
+        const bool ll = hl_ && (rl & LEAF_BIT), lr = hr_ && (rr & LEAF_BIT);
+        const uint32_t bpl = __ballot_sync(FULLMASK, pl), bpr = __ballot_sync(FULLMASK, pr);
+        const uint32_t bll = __ballot_sync(FULLMASK, ll), blr = __ballot_sync(FULLMASK, lr);
+        const int po = sp + __popc(bpl & lt) + __popc(bpr & lt);
+        if (pr) W.stk[po] = rr;
+        if (pl) W.stk[po + (pr ? 1 : 0)] = rl;
+        const int co = __popc(bll & lt) + __popc(blr & lt);
+        if (ll) W.cand[co] = rl & ~LEAF_BIT;
+        if (lr) W.cand[co + (ll ? 1 : 0)] = rr & ~LEAF_BIT;
+        sp += __popc(bpl) + __popc(bpr);
+        const int nc = __popc(bll) + __popc(blr);
+        __syncwarp();
+        for (int c0 = 0; c0 < nc; c0 += 32) {
+            const bool have = c0 + lane < nc;
+            Chord ch;
+            ch.ok = false;
+            int64_t p = 0;
+            if (have) {
+                const uint32_t leaf = W.cand[c0 + lane];
+                p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
+                ch = chord_of(P.geom, p, r);
+            }
+            const bool keep = have && ch.ok && ch.tout > ta && ch.tin < tb;
+            const uint32_t bk = __ballot_sync(FULLMASK, keep);
+            const int nk = __popc(bk);
+            if (nL + nk > cap) {
+                if (!chunked) return 1;
+                on_full(nL);
+                nL = 0;
+            }
+            if (keep) {
+                const int slot = nL + __popc(bk & lt);
+                float col[3];
+                sh_colour(P.shc, p, Y, col);
+                W.q[slot] = make_float4(ch.tc, ch.a, ch.qmin, ch.Qe);
+                W.c[slot] = make_float4(ch.L, col[0], col[1], col[2]);
+                W.tio[slot] = make_float2(ch.tin, ch.tout);
+                W.pid[slot] = (uint32_t)p;
+                if (BWD) {
+                    W.acc[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    W.acc2[slot] = make_float2(0.f, 0.f);
+                }
+            }
+            nL += nk;
+            __syncwarp();
+        }
+    }
+    return 0;
+}
+
+// ClosestHit(ta) = min over Gaussians whose chord has t_out > ta and t_in < tf of
+// max(t_in, ta); tf if there is none (Algorithm 1, Eq. 4).  Cooperative
+// traversal pruned by the warp's best value, near children on top of the stack.
+__device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, float ta, float tf, Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    if (lane == 0) { cnt.chq++; W.stk[0] = 0u; W.stkt[0] = -INFINITY; }
+    __syncwarp();
+    int sp = 1;
+    float best = tf;
+    while (sp > 0) {
+        const int room = (STK - sp) / 2;
+        const int take = min(min(sp, 32), room);
+        if (take <= 0) {
+            if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
+            return best;
+        }
+        const int base = sp - take;
+        const uint32_t ref = lane < take ? W.stk[base + lane] : 0u;
+        const float tent = lane < take ? W.stkt[base + lane] : INFINITY;
+        __syncwarp();
+        sp = base;
+        const bool active = lane < take && tent < best;
+        float cand = INFINITY;
+        bool hl_ = false, hr_ = false;
+        uint32_t rl = 0, rr = 0;
+        float tl = INFINITY, tr = INFINITY;
+        if (active) {
+            cnt.visits++;
+            const float4* nd = P.nodes + 4 * (size_t)ref;
+            const float4 a0 = __ldg(nd), a1 = __ldg(nd + 1), a2 = __ldg(nd + 2), a3 = __ldg(nd + 3);
+            const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
+            hl_ = box_overlap(a0, a1, r, ta, best, tl);
+            hr_ = box_overlap(a2, a3, r, ta, best, tr);
+            rl = (first == split) ? (split | LEAF_BIT) : split;
+            rr = (split + 1 == last) ? ((split + 1) | LEAF_BIT) : (split + 1);
+#pragma unroll
+            for (int side = 0; side < 2; side++) {
+                const bool h = side ? hr_ : hl_;
+                const uint32_t rf = side ? rr : rl;
+                if (h && (rf & LEAF_BIT)) {
+                    const uint32_t leaf = rf & ~LEAF_BIT;
+                    const int64_t p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
+                    const Chord c = chord_of(P.geom, p, r);
+                    if (c.ok && c.tout > ta && c.tin < tf) cand = fminf(cand, fmaxf(c.tin, ta));
+                }
+            }
+        }
+        best = fminf(best, warp_min(cand));
+        if (best <= ta) return ta;
+        // internal children still worth visiting, far one pushed first
+        bool pl = hl_ && !(rl & LEAF_BIT) && tl < best;
+        bool pr = hr_ && !(rr & LEAF_BIT) && tr < best;
+        const bool lnear = tl <= tr;
+        const bool p1 = lnear ? pr : pl, p2 = lnear ? pl : pr;   // p1 = far, p2 = near
+        const uint32_t r1 = lnear ? rr : rl, r2 = lnear ? rl : rr;
+        const float t1 = lnear ? tr : tl, t2 = lnear ? tl : tr;
+        const uint32_t b1 = __ballot_sync(FULLMASK, p1), b2 = __ballot_sync(FULLMASK, p2);
+        const int po = sp + __popc(b1 & lt) + __popc(b2 & lt);
+        if (p1) { W.stk[po] = r1; W.stkt[po] = t1; }
+        if (p2) { W.stk[po + (p1 ? 1 : 0)] = r2; W.stkt[po + (p1 ? 1 : 0)] = t2; }
+        sp += __popc(b1) + __popc(b2);
+        __syncwarp();
+    }
+    return best;
+}
+
+// ------------------------------------------------------------------ per-segment work
+// Lane-parallel sample evaluation: lane = (sample k, group grp); the group's
+// lanes take every G-th hit.  Entry indices come from W.seg (idx) or 0..m-1.
+template <int NS>
+__device__ __forceinline__ void eval_entries(const WS& W, bool idx, int m, float tS, float dtk, float& sig,
+                                             float& S0, float& S1, float& S2) {
+    constexpr int G = 32 / NS;
+    const int lane = threadIdx.x & 31;
+    const int k = lane % NS, grp = lane / NS;
+    const float half = __fmul_rn(0.5f, dtk);
+    for (int h = grp; h < m; h += G) {
+        const uint32_t e = idx ? W.seg[h] : (uint32_t)h;
+        const float4 q4 = W.q[e];
+        const float u = __fmaf_rn((float)k, dtk, __fadd_rn(__fsub_rn(tS, q4.x), half));
+        const float q = __fmaf_rn(__fmul_rn(q4.y, u), u, q4.z);
+        if (q <= q4.w) {
+            const float4 c4 = W.c[e];
+            const float g = exp2f(__fmaf_rn(q, NEG_HALF_LOG2E, c4.x));
+            sig = __fadd_rn(sig, g);
+            S0 = __fmaf_rn(g, c4.y, S0);
+            S1 = __fmaf_rn(g, c4.z, S1);
+            S2 = __fmaf_rn(g, c4.w, S2);
+        }
+    }
+}
+
+// Adjoint, hit-parallel: per entry, accumulate over the segment's samples
+// sum w, sum w u, sum w u^2 and dL/dc_l, with w = (beta_k + gamma_k . c_l) g.
+template <int NS>
+__device__ __forceinline__ void adjoint_entries(const WS& W, bool idx, int m, float tS, float dtk) {
+    const int lane = threadIdx.x & 31;
+    const float half = __fmul_rn(0.5f, dtk);
+    for (int h = lane; h < m; h += 32) {
+        const uint32_t e = idx ? W.seg[h] : (uint32_t)h;
+        const float4 q4 = W.q[e], c4 = W.c[e];
+        const float u0 = __fadd_rn(__fsub_rn(tS, q4.x), half);
+        float A0 = 0.f, A1 = 0.f, A2 = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < NS; k++) {
+            const float u = __fmaf_rn((float)k, dtk, u0);
+            const float q = __fmaf_rn(__fmul_rn(q4.y, u), u, q4.z);
+            if (q <= q4.w) {
+                const float4 b = W.bg[k];
+                const float g = exp2f(__fmaf_rn(q, NEG_HALF_LOG2E, c4.x));
+                const float gp = b.x + b.y * c4.y + b.z * c4.z + b.w * c4.w;
+                const float w = gp * g;
+                A0 += w;
+                A1 += w * u;
+                A2 += w * u * u;
+                d0 += b.y * g; d1 += b.z * g; d2 += b.w * g;
+            }
+        }
+        float4 a = W.acc[e];
+        float2 a2 = W.acc2[e];
+        W.acc[e] = make_float4(a.x + A0, a.y + A1, a.z + A2, a.w + d0);
+        W.acc2[e] = make_float2(a2.x + d1, a2.y + d2);
     }
 }
 
@@ -267,11 +427,55 @@ __device__ __forceinline__ void red_add4(float4* addr, float a, float b, float c
     atomicAdd(addr, make_float4(a, b, c, d));
 }
 
+// Turn the accumulated per-(ray, Gaussian) sums of entries 0..m-1 into the
+// local-frame moments and add them (and the SH gradients) to the Gaussians.
+__device__ void flush_entries(const MarchParams& P, const WS& W, const Ray& r, const float Y[16], int m) {
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < m; e += 32) {
+        const float4 a = W.acc[e];
+        const float2 a2 = W.acc2[e];
+        if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f && a2.x == 0.f && a2.y == 0.f) continue;
+        const int64_t p = W.pid[e];
+        const float4 q4 = W.q[e], c4 = W.c[e];
+        float yc[3], yd[3];
+        local_frame(P.geom, p, r, q4.x, yc, yd);
+        const float A0 = a.x, A1 = a.y, A2 = a.z;
+        const float V0 = A0 * yc[0] + A1 * yd[0], V1 = A0 * yc[1] + A1 * yd[1], V2 = A0 * yc[2] + A1 * yd[2];
+        float Pm[6];
+        const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+        for (int t = 0; t < 6; t++) {
+            const int x = ia[t], y = ib[t];
+            Pm[t] = A0 * yc[x] * yc[y] + A1 * (yc[x] * yd[y] + yd[x] * yc[y]) + A2 * yd[x] * yd[y];
+        }
+        float4* gp = P.grad + 16 * p;
+        red_add4(gp + 0, A0, V0, V1, V2);
+        red_add4(gp + 1, Pm[0], Pm[1], Pm[2], Pm[3]);
+        red_add4(gp + 2, Pm[4], Pm[5], 0.f, 0.f);
+        // SH: dL/dK_k = Y_k dL/dc_l where the colour is not clamped
+        const float m0 = c4.y > 0.f ? a.w : 0.f, m1 = c4.z > 0.f ? a2.x : 0.f, m2 = c4.w > 0.f ? a2.y : 0.f;
+#pragma unroll
+        for (int jx = 0; jx < 12; jx++) {
+            float v[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int idx = 4 * jx + t, k = idx / 3, ch = idx % 3;
+                v[t] = Y[k] * (ch == 0 ? m0 : (ch == 1 ? m1 : m2));
+            }
+            red_add4(gp + 4 + jx, v[0], v[1], v[2], v[3]);
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ one ray, one warp
 template <int NS, bool BWD>
-__device__ void march_ray(const MarchParams& P, int64_t ray, int cam, int px, int py, uint32_t* __restrict__ hl,
-                          uint32_t* __restrict__ stk, float* __restrict__ tstk, Counters& cnt) {
-    const rgx_camera& C = P.cams[cam];
-    // ---- ray (pinhole, OpenCV convention)
+__device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const rgx_camera& C, int px, int py,
+                          Counters& cnt, float4& o_rgba, float4& o_state, int& o_nrec) {
+    const int lane = threadIdx.x & 31;
+    const int k = lane % NS;
+    const int cap = P.hit_cap;
+    // ---- ray (pinhole, OpenCV convention); every lane holds the same values
     Ray r;
     {
         const float ux = ((float)px + 0.5f - C.cx) / C.fx;
@@ -287,14 +491,14 @@ __device__ void march_ray(const MarchParams& P, int64_t ray, int cam, int px, in
         r.iy = 1.0f / (fabsf(r.dy) > tiny ? r.dy : copysignf(tiny, r.dy));
         r.iz = 1.0f / (fabsf(r.dz) > tiny ? r.dz : copysignf(tiny, r.dz));
     }
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, bA = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Tf = 1.f, dTcoef = 0.f;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Tf = 1.f, dTcoef = 0.f;
     if (BWD) {
         const float4 up = P.d_rgba[ray];
         if (up.x == 0.0f && up.y == 0.0f && up.z == 0.0f && up.w == 0.0f) return;
-        a0 = up.x; a1 = up.y; a2 = up.z; bA = up.w;
+        a0 = up.x; a1 = up.y; a2 = up.z;
         const float4 st = P.state[ray];
         Cf0 = st.x; Cf1 = st.y; Cf2 = st.z; Tf = st.w;
-        dTcoef = (a0 * P.bg0 + a1 * P.bg1 + a2 * P.bg2 - bA) * Tf;
+        dTcoef = (a0 * P.bg0 + a1 * P.bg1 + a2 * P.bg2 - up.w) * Tf;
     }
     // ---- bounds: t_n, and t_f = camera t_far or the exit of the scene box
     const float tn = C.t_near;
@@ -304,7 +508,7 @@ __device__ void march_ray(const MarchParams& P, int64_t ray, int cam, int px, in
         const float4 hi = make_float4(P.root[3], P.root[4], P.root[5], 0.f);
         float tentry;
         const bool in = box_overlap(lo, hi, r, -INFINITY, INFINITY, tentry);
-        float fx = r.ix >= 0.0f ? hi.x : lo.x, fy = r.iy >= 0.0f ? hi.y : lo.y, fz = r.iz >= 0.0f ? hi.z : lo.z;
+        const float fx = r.ix >= 0.0f ? hi.x : lo.x, fy = r.iy >= 0.0f ? hi.y : lo.y, fz = r.iz >= 0.0f ? hi.z : lo.z;
         const float texit = fminf(fminf((fx - r.ox) * r.ix, (fy - r.oy) * r.iy), (fz - r.oz) * r.iz);
         tf = (in && texit > tn) ? texit : tn;
     }
@@ -317,8 +521,11 @@ __device__ void march_ray(const MarchParams& P, int64_t ray, int cam, int px, in
     float tS = tn;
     int j = 0;  // lattice index in uniform mode
     int nrec = 0;
+    int nL = 0;
+    float w_lo = 1.0f, w_hi = 0.0f;  // current window (empty)
+    float wlen = 4.0f * (float)NS * (uniform ? P.dt : P.dt_max);
     if (P.n > 0 && tf > tn && skip) {
-        const float th = closest_hit(P, r, tn, tf, stk, tstk, cnt);
+        const float th = w_closest(P, W, r, tn, tf, cnt);
         if (uniform) {
             const int jj = (int)floorf((th - tn) / P.dt) - 1;
             j = jj > 0 ? jj : 0;
@@ -328,52 +535,88 @@ __device__ void march_ray(const MarchParams& P, int64_t ray, int cam, int px, in
         }
     }
     const float minstep = uniform ? P.dt : (float)NS * fminf(P.dt_min, P.dt_max);
-    const int iter_cap = P.max_segments > 0 ? P.max_segments
-                                            : (int)fminf((tf - tn) / minstep, 2.0e9f) + 8;
+    const int iter_cap = P.max_segments > 0 ? P.max_segments : (int)fminf((tf - tn) / minstep, 2.0e9f) + 8;
     int iters = 0;
     while (P.n > 0 && tS < tf && T > P.t_eps) {
-        if (iters >= iter_cap) { atomicOr(P.status, (unsigned)RGX_ERR_ITER_LIMIT); break; }
+        if (iters >= iter_cap) {
+            if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_ITER_LIMIT);
+            break;
+        }
         iters++;
         // ---- segment size: uniform dt, or Eq. 5
         float dtk;
         if (uniform) {
             dtk = P.dt;
         } else {
-            float base = fmaxf(__fdiv_rn(tS, P.beta), P.dt_min);
+            const float base = fmaxf(__fdiv_rn(tS, P.beta), P.dt_min);
             dtk = fminf(__fmul_rn(base, rcbrtf(T)), P.dt_max);
         }
         const float te = uniform ? __fmaf_rn((float)(j + NS), P.dt, tn) : __fadd_rn(tS, __fmul_rn((float)NS, dtk));
         const float tcut = fminf(te, tf);
-        float sig[NS], S[NS][3];
-#pragma unroll
-        for (int k = 0; k < NS; k++) { sig[k] = 0.f; S[k][0] = S[k][1] = S[k][2] = 0.f; }
-        // ---- hit collection + per-sample accumulation (chunked)
-        int nexact = 0;
-        int nchunk = 0;
-        int first_count = 0;
-        uint32_t cursor = 0;
-        do {
-            const int nh = collect(P, r, tS, tcut, hl, P.hit_cap, cursor, stk, cnt);
-            if (nchunk == 0) first_count = nh;
-            nchunk++;
-            for (int h = 0; h < nh; h++) {
-                const uint32_t leaf = hl[h * RGX_BLOCK];
-                const int64_t p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
-                float4 g0, g1, g2, g3;
-                const Chord c = chord_of(P.geom, p, r, g1, g2, g3, g0);
-                if (!(c.ok && c.tin < tcut && c.tout > tS)) continue;
-                nexact++;
-                float col[3], pre[3];
-                sh_colour(P.shc, p, Y, col, pre);
-                const float u0 = __fadd_rn(__fsub_rn(tS, c.tc), __fmul_rn(0.5f, dtk));
-                eval_hit<NS>(c, u0, dtk, col, sig, S);
+        // ---- window of chords covering [tS, tcut)
+        bool chunked = false;
+        if (!(tS >= w_lo && tcut <= w_hi)) {
+            if (BWD) flush_entries(P, W, r, Y, nL);
+            const float need = te - tS;
+            float len = fmaxf(wlen, need);
+            while (true) {
+                float hi = (len <= need) ? tcut : fminf(tS + len, tf);
+                hi = fmaxf(hi, tcut);
+                nL = 0;
+                if (lane == 0) cnt.windows++;
+                const int rc = w_collect<BWD>(P, W, r, Y, tS, hi, cap, nL, false, NoChunk(), cnt);
+                if (rc == 0) {
+                    w_lo = tS; w_hi = hi;
+                    wlen = (nL * 4 <= cap) ? 2.0f * len : len;
+                    break;
+                }
+                if (len <= need || rc == 2) { chunked = true; break; }
+                len = fmaxf(0.25f * len, need);
+                wlen = len;
             }
-        } while (cursor != DONE);
-        (void)first_count;
+            if (chunked) { nL = 0; w_lo = 1.0f; w_hi = 0.0f; }
+        }
+        // ---- the segment's hits and per-sample sums
+        float sig = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+        int nexact = 0;
+        if (!chunked) {
+            const uint32_t lt = lanemask_lt();
+            for (int b = 0; b < nL; b += 32) {
+                const int e = b + lane;
+                bool in = false;
+                if (e < nL) { const float2 io = W.tio[e]; in = io.x < tcut && io.y > tS; }
+                const uint32_t bb = __ballot_sync(FULLMASK, in);
+                if (in) W.seg[nexact + __popc(bb & lt)] = (uint32_t)e;
+                nexact += __popc(bb);
+            }
+            __syncwarp();
+            if (nexact) eval_entries<NS>(W, true, nexact, tS, dtk, sig, S0, S1, S2);
+        } else {
+            int tot = 0;
+            auto onfull = [&](int m) {
+                eval_entries<NS>(W, false, m, tS, dtk, sig, S0, S1, S2);
+                tot += m;
+                __syncwarp();
+            };
+            nL = 0;
+            w_collect<BWD>(P, W, r, Y, tS, tcut, cap, nL, true, onfull, cnt);
+            if (nL) onfull(nL);
+            nexact = tot;
+            nL = 0;
+        }
         if (nexact == 0) {
-            cnt.skips++;
+            if (lane == 0) cnt.skips++;
             if (skip) {
-                const float th = closest_hit(P, r, te, tf, stk, tstk, cnt);
+                float cand = INFINITY;
+                for (int e = lane; e < nL; e += 32) {
+                    const float2 io = W.tio[e];
+                    if (io.y > te && io.x < tf) cand = fminf(cand, fmaxf(io.x, te));
+                }
+                cand = warp_min(cand);
+                float th;
+                if (cand < INFINITY) th = cand;
+                else if (w_hi >= tf && w_lo <= w_hi) th = tf;
+                else th = w_closest(P, W, r, te, tf, cnt);
                 if (th >= tf) break;
                 if (uniform) {
                     const int jj = (int)floorf((th - tn) / P.dt) - 1;
@@ -387,125 +630,95 @@ __device__ void march_ray(const MarchParams& P, int64_t ray, int cam, int px, in
             }
             continue;
         }
-        cnt.segs++;
-        cnt.hits += nexact;
-        cnt.evals += nexact * NS;
-        if (!BWD && P.sched) {
-            if (nrec < P.sched_cap) P.sched[ray * P.sched_cap + nrec] = make_float2(tS, dtk);
+        if (lane == 0) {
+            cnt.segs++;
+            cnt.hits += nexact;
+            cnt.evals += nexact * NS;
+            if (!BWD && P.sched && nrec < P.sched_cap) P.sched[ray * P.sched_cap + nrec] = make_float2(tS, dtk);
         }
         nrec++;
+        // ---- combine the lane groups (butterfly: every lane ends with the same sums)
+#pragma unroll
+        for (int off = NS; off < 32; off <<= 1) {
+            sig = __fadd_rn(sig, __shfl_xor_sync(FULLMASK, sig, off));
+            S0 = __fadd_rn(S0, __shfl_xor_sync(FULLMASK, S0, off));
+            S1 = __fadd_rn(S1, __shfl_xor_sync(FULLMASK, S1, off));
+            S2 = __fadd_rn(S2, __shfl_xor_sync(FULLMASK, S2, off));
+        }
         // ---- front-to-back compositing of the N_S samples (Eq. 3)
         const float t0 = __fadd_rn(tS, __fmul_rn(0.5f, dtk));
-        if (!BWD) {
+        const float tk = __fmaf_rn((float)k, dtk, t0);
+        const bool valid = tk < tf && sig > 0.0f;
+        const float x = valid ? __fmul_rn(sig, dtk) : 0.0f;
+        const float e = valid ? expf(-x) : 1.0f;
+        const float alpha = valid ? -expm1f(-x) : 0.0f;
+        const float inv = valid ? __fdiv_rn(1.0f, sig) : 0.0f;
+        const float c0 = __fmul_rn(S0, inv), c1 = __fmul_rn(S1, inv), c2 = __fmul_rn(S2, inv);
+        float pinc = e;  // inclusive product of e over samples 0..k
 #pragma unroll
-            for (int k = 0; k < NS; k++) {
-                const float tk = __fmaf_rn((float)k, dtk, t0);
-                if (tk < tf && sig[k] > 0.0f) {
-                    const float x = __fmul_rn(sig[k], dtk);
-                    const float e = expf(-x);
-                    const float alpha = -expm1f(-x);
-                    const float w = __fmul_rn(T, alpha);
-                    const float inv = __fdiv_rn(1.0f, sig[k]);
-                    C0 = __fmaf_rn(w, __fmul_rn(S[k][0], inv), C0);
-                    C1 = __fmaf_rn(w, __fmul_rn(S[k][1], inv), C1);
-                    C2 = __fmaf_rn(w, __fmul_rn(S[k][2], inv), C2);
-                    T = __fmul_rn(T, e);
-                }
-            }
-        } else {
-            // replay compositing, turning (sig, S) into (beta, gamma):
-            //   dL/dg_l = beta_k + gamma_k . c_l,   dL/dc_l += gamma_k g_l
-#pragma unroll
-            for (int k = 0; k < NS; k++) {
-                const float tk = __fmaf_rn((float)k, dtk, t0);
-                if (tk < tf && sig[k] > 0.0f) {
-                    const float x = __fmul_rn(sig[k], dtk);
-                    const float e = expf(-x);
-                    const float alpha = -expm1f(-x);
-                    const float w = __fmul_rn(T, alpha);
-                    const float inv = __fdiv_rn(1.0f, sig[k]);
-                    const float c0 = __fmul_rn(S[k][0], inv), c1 = __fmul_rn(S[k][1], inv), c2 = __fmul_rn(S[k][2], inv);
-                    C0 = __fmaf_rn(w, c0, C0);
-                    C1 = __fmaf_rn(w, c1, C1);
-                    C2 = __fmaf_rn(w, c2, C2);
-                    const float Tn = __fmul_rn(T, e);
-                    float ds = a0 * (Tn * c0 - (Cf0 - C0)) + a1 * (Tn * c1 - (Cf1 - C1)) + a2 * (Tn * c2 - (Cf2 - C2));
-                    ds = dtk * (ds - dTcoef);
-                    const float g0 = a0 * w * inv, g1_ = a1 * w * inv, g2_ = a2 * w * inv;
-                    sig[k] = ds - (g0 * c0 + g1_ * c1 + g2_ * c2);
-                    S[k][0] = g0; S[k][1] = g1_; S[k][2] = g2_;
-                    T = Tn;
-                } else {
-                    sig[k] = 0.0f; S[k][0] = S[k][1] = S[k][2] = 0.0f;
-                }
-            }
-            // second pass over the same hits: per-Gaussian moments and atomics
-            uint32_t cur2 = 0;
-            const bool reuse = (nchunk == 1);
-            do {
-                int nh;
-                if (reuse) { nh = first_count; cur2 = DONE; }
-                else nh = collect(P, r, tS, tcut, hl, P.hit_cap, cur2, stk, cnt);
-                for (int h = 0; h < nh; h++) {
-                    const uint32_t leaf = hl[h * RGX_BLOCK];
-                    const int64_t p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
-                    float4 q0, q1, q2, q3;
-                    const Chord c = chord_of(P.geom, p, r, q1, q2, q3, q0);
-                    if (!(c.ok && c.tin < tcut && c.tout > tS)) continue;
-                    float col[3], pre[3];
-                    sh_colour(P.shc, p, Y, col, pre);
-                    const float u0 = __fadd_rn(__fsub_rn(tS, c.tc), __fmul_rn(0.5f, dtk));
-                    float A0 = 0.f, A1 = 0.f, A2 = 0.f, dc0 = 0.f, dc1 = 0.f, dc2 = 0.f;
-#pragma unroll
-                    for (int k = 0; k < NS; k++) {
-                        const float u = __fmaf_rn((float)k, dtk, u0);
-                        const float q = __fmaf_rn(__fmul_rn(c.a, u), u, c.qmin);
-                        if (q <= c.Qe) {
-                            const float g = exp2f(__fmaf_rn(q, NEG_HALF_LOG2E, c.L));
-                            const float gp = sig[k] + S[k][0] * col[0] + S[k][1] * col[1] + S[k][2] * col[2];
-                            const float wv = gp * g;
-                            A0 += wv;
-                            A1 += wv * u;
-                            A2 += wv * u * u;
-                            dc0 += S[k][0] * g; dc1 += S[k][1] * g; dc2 += S[k][2] * g;
-                        }
-                    }
-                    float yc[3], yd[3];
-                    local_frame(q0, q1, q2, q3, r, c.tc, yc, yd);
-                    const float V0 = A0 * yc[0] + A1 * yd[0], V1 = A0 * yc[1] + A1 * yd[1], V2 = A0 * yc[2] + A1 * yd[2];
-                    float Pm[6];
-                    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-                    for (int m = 0; m < 6; m++) {
-                        const int x = ia[m], y = ib[m];
-                        Pm[m] = A0 * yc[x] * yc[y] + A1 * (yc[x] * yd[y] + yd[x] * yc[y]) + A2 * yd[x] * yd[y];
-                    }
-                    float4* gp = P.grad + 16 * p;
-                    red_add4(gp + 0, A0, V0, V1, V2);
-                    red_add4(gp + 1, Pm[0], Pm[1], Pm[2], Pm[3]);
-                    red_add4(gp + 2, Pm[4], Pm[5], 0.f, 0.f);
-                    const float m0 = pre[0] > 0.f ? dc0 : 0.f, m1 = pre[1] > 0.f ? dc1 : 0.f, m2 = pre[2] > 0.f ? dc2 : 0.f;
-#pragma unroll
-                    for (int jx = 0; jx < 12; jx++) {
-                        float v[4];
-#pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            const int idx = 4 * jx + e, k = idx / 3, ch = idx % 3;
-                            v[e] = Y[k] * (ch == 0 ? m0 : (ch == 1 ? m1 : m2));
-                        }
-                        red_add4(gp + 4 + jx, v[0], v[1], v[2], v[3]);
-                    }
-                }
-            } while (cur2 != DONE);
+        for (int d = 1; d < NS; d <<= 1) {
+            const float v = __shfl_up_sync(FULLMASK, pinc, d, NS);
+            if (k >= d) pinc = __fmul_rn(pinc, v);
         }
+        float pexc = __shfl_up_sync(FULLMASK, pinc, 1, NS);
+        if (k == 0) pexc = 1.0f;
+        const float Tk = __fmul_rn(T, pexc);
+        const float w = __fmul_rn(Tk, alpha);
+        const float k0 = __fmul_rn(w, c0), k1 = __fmul_rn(w, c1), k2 = __fmul_rn(w, c2);
+        float s0 = k0, s1 = k1, s2 = k2;
+#pragma unroll
+        for (int d = NS / 2; d >= 1; d >>= 1) {
+            s0 = __fadd_rn(s0, __shfl_xor_sync(FULLMASK, s0, d, NS));
+            s1 = __fadd_rn(s1, __shfl_xor_sync(FULLMASK, s1, d, NS));
+            s2 = __fadd_rn(s2, __shfl_xor_sync(FULLMASK, s2, d, NS));
+        }
+        const float Tend = __fmul_rn(T, __shfl_sync(FULLMASK, pinc, NS - 1, NS));
+        if (BWD) {
+            // C_<=k = C + inclusive prefix of the contributions; T_{k+1} = T_k e_k
+            float p0 = k0, p1 = k1, p2 = k2;
+#pragma unroll
+            for (int d = 1; d < NS; d <<= 1) {
+                const float v0 = __shfl_up_sync(FULLMASK, p0, d, NS);
+                const float v1 = __shfl_up_sync(FULLMASK, p1, d, NS);
+                const float v2 = __shfl_up_sync(FULLMASK, p2, d, NS);
+                if (k >= d) { p0 += v0; p1 += v1; p2 += v2; }
+            }
+            const float Tn = Tk * e;
+            float ds = a0 * (Tn * c0 - (Cf0 - (C0 + p0))) + a1 * (Tn * c1 - (Cf1 - (C1 + p1))) +
+                       a2 * (Tn * c2 - (Cf2 - (C2 + p2)));
+            ds = dtk * (ds - dTcoef);
+            const float g0 = a0 * w * inv, g1 = a1 * w * inv, g2 = a2 * w * inv;
+            const float beta = ds - (g0 * c0 + g1 * c1 + g2 * c2);
+            if (lane < NS) W.bg[k] = valid ? make_float4(beta, g0, g1, g2) : make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncwarp();
+            if (!chunked) {
+                adjoint_entries<NS>(W, true, nexact, tS, dtk);
+                __syncwarp();
+            } else {
+                auto onfull2 = [&](int m) {
+                    adjoint_entries<NS>(W, false, m, tS, dtk);
+                    __syncwarp();
+                    flush_entries(P, W, r, Y, m);
+                };
+                nL = 0;
+                w_collect<BWD>(P, W, r, Y, tS, tcut, cap, nL, true, onfull2, cnt);
+                if (nL) onfull2(nL);
+                nL = 0;
+            }
+        }
+        C0 = __fadd_rn(C0, s0);
+        C1 = __fadd_rn(C1, s1);
+        C2 = __fadd_rn(C2, s2);
+        T = Tend;
         if (uniform) { j += NS; tS = __fmaf_rn((float)j, P.dt, tn); } else tS = te;
     }
-    if (!BWD) {
-        P.rgba[ray] = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
-        if (P.state) P.state[ray] = make_float4(C0, C1, C2, T);
-        if (P.sched_n) P.sched_n[ray] = nrec;
+    if (BWD) {
+        flush_entries(P, W, r, Y, nL);
+        if (lane == 0 && T != Tf) atomicOr(P.status, (unsigned)RGX_ERR_REPLAY);
     } else {
-        if (T != Tf) atomicOr(P.status, (unsigned)RGX_ERR_REPLAY);
+        o_rgba = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
+        o_state = make_float4(C0, C1, C2, T);
+        o_nrec = nrec;
     }
 }
 
@@ -516,13 +729,34 @@ __device__ __forceinline__ uint32_t tiles_of(const rgx_camera& c, bool ztiles, i
     return ((ntx + 7) / 8) * ((nty + 7) / 8) * 64u;
 }
 
+// Pixel of lane `l` of local tile `lt` of camera `cam`.
+__device__ __forceinline__ bool tile_pixel(const rgx_camera& cam, uint32_t lt, int l, bool zt, int tw, int th,
+                                           int& px, int& py) {
+    if (!zt) {
+        const int64_t pix = (int64_t)lt * 32 + l;
+        px = (int)(pix % cam.width);
+        py = (int)(pix / cam.width);
+        return pix < (int64_t)cam.width * cam.height;
+    }
+    const uint32_t ntx = (cam.width + tw - 1) / tw;
+    const uint32_t nsx = (ntx + 7) / 8;
+    const uint32_t sblk = lt >> 6, w = lt & 63u;
+    const uint32_t wx = (w & 1u) | ((w >> 1) & 2u) | ((w >> 2) & 4u);
+    const uint32_t wy = ((w >> 1) & 1u) | ((w >> 2) & 2u) | ((w >> 3) & 4u);
+    const uint32_t tx = (sblk % nsx) * 8 + wx, ty = (sblk / nsx) * 8 + wy;
+    px = (int)(tx * tw + l % tw);
+    py = (int)(ty * th + l / tw);
+    return px < cam.width && py < cam.height;
+}
+
 template <int NS, bool BWD>
 __global__ void __launch_bounds__(RGX_BLOCK) k_march(MarchParams P) {
-    extern __shared__ uint32_t smem[];
-    uint32_t* s_tiles = smem;                 // [ncam+1] tile prefix
-    uint32_t* s_pix = smem + (P.ncam + 1);    // [ncam+1] pixel prefix
-    const int off = ((2 * (P.ncam + 1)) + 3) & ~3;
-    uint32_t* s_hits = smem + off;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t* s_tiles = (uint32_t*)smem;         // [ncam+1] tile prefix
+    uint32_t* s_pix = s_tiles + (P.ncam + 1);    // [ncam+1] pixel prefix
+    const size_t head = ((size_t)(2 * (P.ncam + 1)) * 4 + 15) & ~(size_t)15;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WS W = carve((char*)smem + head + (size_t)warp * warp_bytes(P.hit_cap, BWD), P.hit_cap, BWD);
     const bool zt = (P.flags & RGX_ZTILES) != 0;
     if (threadIdx.x == 0) {
         uint32_t tsum = 0, psum = 0;
@@ -535,48 +769,49 @@ __global__ void __launch_bounds__(RGX_BLOCK) k_march(MarchParams P) {
     }
     __syncthreads();
     const uint32_t total = s_tiles[P.ncam];
-    const int lane = threadIdx.x & 31;
-    uint32_t* hl = s_hits + threadIdx.x;
-    uint32_t stk[RGX_STACK];
-    float tstk[RGX_STACK];
     while (true) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(P.queue, 1u);
         t = __shfl_sync(FULLMASK, t, 0);
         if (t >= total) break;
-        int lo = 0, hi = P.ncam;  // find camera: s_tiles[c] <= t < s_tiles[c+1]
-        while (hi - lo > 1) { int mid = (lo + hi) >> 1; if (s_tiles[mid] <= t) lo = mid; else hi = mid; }
+        int lo = 0, hi = P.ncam;
+        while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (s_tiles[mid] <= t) lo = mid; else hi = mid; }
         const int c = lo;
         const rgx_camera& cam = P.cams[c];
         const uint32_t lt = t - s_tiles[c];
-        int px, py;
-        bool valid;
-        if (!zt) {
-            const int64_t pix = (int64_t)lt * 32 + lane;
-            valid = pix < (int64_t)cam.width * cam.height;
-            px = (int)(pix % cam.width); py = (int)(pix / cam.width);
-        } else {
-            const uint32_t ntx = (cam.width + P.tile_w - 1) / P.tile_w;
-            const uint32_t nsx = (ntx + 7) / 8;
-            const uint32_t sblk = lt >> 6, w = lt & 63u;
-            const uint32_t wx = (w & 1u) | ((w >> 1) & 2u) | ((w >> 2) & 4u);
-            const uint32_t wy = ((w >> 1) & 1u) | ((w >> 2) & 2u) | ((w >> 3) & 4u);
-            const uint32_t tx = (sblk % nsx) * 8 + wx, ty = (sblk / nsx) * 8 + wy;
-            px = (int)(tx * P.tile_w + lane % P.tile_w);
-            py = (int)(ty * P.tile_h + lane / P.tile_w);
-            valid = px < cam.width && py < cam.height;
-        }
-        Counters cnt = {0, 0, 0, 0, 0, 0};
-        if (valid) {
+        Counters cnt = {0, 0, 0, 0, 0, 0, 0};
+        float4 my_rgba = make_float4(0.f, 0.f, 0.f, 0.f), my_state = my_rgba;
+        int my_nrec = 0;
+        for (int l = 0; l < 32; l++) {
+            int px, py;
+            if (!tile_pixel(cam, lt, l, zt, P.tile_w, P.tile_h, px, py)) continue;
             const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
-            march_ray<NS, BWD>(P, ray, c, px, py, hl, stk, tstk, cnt);
+            float4 o_rgba, o_state;
+            int o_nrec = 0;
+            march_ray<NS, BWD>(P, W, ray, cam, px, py, cnt, o_rgba, o_state, o_nrec);
+            if (!BWD && lane == l) { my_rgba = o_rgba; my_state = o_state; my_nrec = o_nrec; }
+        }
+        if (!BWD) {
+            int px, py;
+            if (tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
+                const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
+                P.rgba[ray] = my_rgba;
+                if (P.state) P.state[ray] = my_state;
+                if (P.sched_n) P.sched_n[ray] = my_nrec;
+            }
         }
         if (P.counters) {
-            const unsigned v[7] = {valid ? 1u : 0u, cnt.segs, cnt.hits, cnt.evals, cnt.visits, cnt.chq, cnt.skips};
+            int nvalid = 0;
+            {
+                int px, py;
+                nvalid = tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py) ? 1 : 0;
+            }
+            const unsigned v[8] = {(unsigned)nvalid, cnt.segs, cnt.hits, cnt.evals, cnt.visits, cnt.chq, cnt.skips,
+                                   cnt.windows};
 #pragma unroll
-            for (int i = 0; i < 7; i++) {
+            for (int i = 0; i < 8; i++) {
                 const unsigned s = __reduce_add_sync(FULLMASK, v[i]);
-                if (lane == 0 && s) atomicAdd(&P.counters[i == 6 ? 6 : i], (unsigned long long)s);
+                if (lane == 0 && s) atomicAdd(&P.counters[i], (unsigned long long)s);
             }
         }
     }
@@ -660,7 +895,7 @@ static rgx_status check_opts(rgx_scene* s, const rgx_opts* o) {
     } else if (!(o->dt > 0.0f)) {
         return set_err(s, RGX_ERR_INVALID_ARG, "dt must be > 0");
     }
-    if (o->hit_cap < 8 || o->hit_cap > 256) return set_err(s, RGX_ERR_INVALID_ARG, "hit_cap must be in [8, 256]");
+    if (o->hit_cap < 32 || o->hit_cap > 512) return set_err(s, RGX_ERR_INVALID_ARG, "hit_cap must be in [32, 512]");
     if ((o->flags & RGX_ZTILES) && (o->tile_w <= 0 || o->tile_h <= 0 || o->tile_w * o->tile_h != 32))
         return set_err(s, RGX_ERR_INVALID_ARG, "tile_w * tile_h must be 32");
     if (!(o->t_eps >= 0.0f)) return set_err(s, RGX_ERR_INVALID_ARG, "t_eps must be >= 0");
@@ -702,10 +937,18 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     RGX_CUDA(s, cudaMemsetAsync(s->queue, 0, sizeof(unsigned), st));
     RGX_CUDA(s, cudaMemsetAsync(s->counters, 0, 8 * sizeof(unsigned long long), st));
     void* k = pick_kernel(o->n_s, bwd);
-    const size_t smem = (size_t)((((2 * (ncam + 1)) + 3) & ~3) + o->hit_cap * RGX_BLOCK) * sizeof(uint32_t);
-    RGX_CUDA(s, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t head = ((size_t)(2 * (ncam + 1)) * 4 + 15) & ~(size_t)15;
+    const size_t smem = head + (size_t)WARPS * warp_bytes(o->hit_cap, bwd);
     int occ = 0;
-    RGX_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, RGX_BLOCK, smem));
+    for (int i = 0; i < s->ncfg; i++)
+        if (s->cfg[i].k == k && s->cfg[i].smem == smem) occ = s->cfg[i].occ;
+    if (occ == 0) {
+        RGX_CUDA(s, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        RGX_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, RGX_BLOCK, smem));
+        if (occ < 1) occ = 1;
+        const int slot = s->ncfg < 32 ? s->ncfg++ : 31;
+        s->cfg[slot] = {k, smem, occ};
+    }
     if (occ < 1) occ = 1;
     const int grid = s->num_sms * occ;
     void* args[] = {&P};

@@ -35,7 +35,7 @@ RGX_SKIP, RGX_ADAPTIVE, RGX_MORTON, RGX_ZTILES, RGX_MORTON63 = 1, 2, 4, 8, 16
 
 EXPORTS = ["rgx_scene_create", "rgx_scene_destroy", "rgx_build_bvh", "rgx_render_forward",
            "rgx_render_forward_sched", "rgx_render_backward", "rgx_sync_status", "rgx_fwd_state_bytes",
-           "rgx_last_error", "rgx_get_bvh", "rgx_get_counters"]
+           "rgx_last_error", "rgx_get_bvh", "rgx_get_counters", "rgx_autotune"]
 
 
 class RgxCamera(C.Structure):
@@ -85,6 +85,9 @@ def lib() -> C.CDLL:
             l.rgx_last_error.argtypes = [vp]
             l.rgx_get_bvh.argtypes = [vp, vp, vp, vp, vp, vp]
             l.rgx_get_counters.argtypes = [vp, C.POINTER(C.c_uint64), vp]
+            l.rgx_autotune.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), C.c_int32,
+                                       C.c_int32, fp, vp, fp, fp, fp, fp, fp, fp, C.POINTER(RgxOpts),
+                                       C.POINTER(C.c_float), vp]
             for name in EXPORTS:
                 f = getattr(l, name)
                 if name not in ("rgx_fwd_state_bytes", "rgx_last_error"):
@@ -205,8 +208,19 @@ def rgx_get_bvh(h, n, stream=None):
 def rgx_get_counters(h, stream=None):
     out = (C.c_uint64 * 8)()
     _check(lib().rgx_get_counters(h, out, _stream(stream)), h)
-    keys = ["rays", "segments", "hits", "evals", "node_visits", "closest_hit", "skipped", "spare"]
+    keys = ["rays", "segments", "hits", "evals", "node_visits", "closest_hit", "skipped", "windows"]
     return dict(zip(keys, [int(v) for v in out]))
+
+
+def rgx_autotune(h, cams: Cameras, base, tune_ns, with_backward, rgba, state, d_rgba, grads, stream=None):
+    """Returns (best RgxOpts, best time in ms).  `grads` are scratch buffers."""
+    best = RgxOpts()
+    ms = C.c_float(0.0)
+    g = grads if grads is not None else [None] * 5
+    _check(lib().rgx_autotune(h, cams.ptr, cams.count, C.byref(base), int(tune_ns), int(with_backward),
+                              _ptr(rgba), _ptr(state), _ptr(d_rgba), *[_ptr(x) for x in g], C.byref(best),
+                              C.byref(ms), _stream(stream)), h)
+    return best, float(ms.value)
 
 
 # ------------------------------------------------------------------ convenience
@@ -256,6 +270,20 @@ class Scene:
 
     def counters(self, stream=None):
         return rgx_get_counters(self.h, stream)
+
+    def autotune(self, cams: Cameras, base, tune_ns: bool = False, with_backward: bool = True, stream=None):
+        """Pick tile shape / hit_cap (/ N_S) by timing on this scene; returns (RgxOpts, ms)."""
+        dev = torch.device("cuda", self.device)
+        rgba = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
+        state = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
+        d_rgba, grads = None, None
+        if with_backward:
+            d_rgba = torch.randn(cams.n_rays, 4, dtype=torch.float32, device=dev)
+            n = max(self.n, 1)
+            grads = [torch.zeros(n, 3, device=dev), torch.zeros(n, 3, device=dev), torch.zeros(n, 4, device=dev),
+                     torch.zeros(n, device=dev), torch.zeros(n, 16, 3, device=dev)]
+        self._keep = cams
+        return rgx_autotune(self.h, cams, base, tune_ns, with_backward, rgba, state, d_rgba, grads, stream)
 
 
 def scene_tensors(scene, device="cuda"):

@@ -4,8 +4,8 @@
   reproduces every ray's T_final bit for bit (no RGX_ERR_REPLAY);
 * Z-order storage (RGX_MORTON) and Z-order ray tiles (RGX_ZTILES) change memory
   order only: results are bit-identical with and without them;
-* hit lists are chunked, never dropped: hit_cap 8 and 256 give bit-identical
-  results;
+* chord lists are windowed / chunked, never dropped: hit_cap 32 and 512 agree
+  to float32 rounding;
 * several cameras in one persistent launch equal one launch per camera;
 * edge cases: empty scene -> background; a single Gaussian; ragged image
   sizes; host-side option checks; bad parameters and the segment limit
@@ -48,15 +48,19 @@ def test_memory_order_options_are_bit_identical(flag):
     np.testing.assert_array_equal(a["rgba"], b["rgba"])
 
 
-def test_hit_cap_chunking_is_exact():
+def test_hit_cap_chunking_never_drops_hits():
+    # hit_cap sets the chord-window capacity; 32 forces windows down to single
+    # segments and chunked segments.  Summation order may change (float32
+    # rounding) but no hit may be lost.
     w = synth.workload("torus_100k", n=60000, scale_res=0.2)
-    a = gpu_render(w.scene, w.cameras, opts_with(w.options, hit_cap=8))
-    b = gpu_render(w.scene, w.cameras, opts_with(w.options, hit_cap=256))
-    np.testing.assert_array_equal(a["rgba"], b["rgba"])
+    a = gpu_render(w.scene, w.cameras, opts_with(w.options, hit_cap=32))
+    b = gpu_render(w.scene, w.cameras, opts_with(w.options, hit_cap=512))
+    assert a["status"] == 0 and b["status"] == 0
+    np.testing.assert_allclose(a["rgba"], b["rgba"], rtol=0, atol=2e-6)
     d = np.random.default_rng(1).normal(size=a["rgba"].shape)
     ga, gb = gpu_backward(a, d), gpu_backward(b, d)
     for k in ("means", "scales", "quats", "densities", "sh"):
-        np.testing.assert_allclose(ga[k], gb[k], rtol=1e-4, atol=1e-6 * np.abs(gb[k]).max())
+        np.testing.assert_allclose(ga[k], gb[k], rtol=1e-3, atol=1e-4 * np.abs(gb[k]).max())
 
 
 def test_batch_launch_equals_single_launches():
@@ -88,7 +92,7 @@ def test_invalid_options_rejected_on_host():
     t = rgx.scene_tensors(w.scene)
     sc.build(*t, rgx.make_opts(w.options))
     cb = rgx.Cameras(w.cameras)
-    for bad in (dict(n_s=5), dict(dt=0.0), dict(hit_cap=1), dict(ztiles=True, tile_w=5, tile_h=5)):
+    for bad in (dict(n_s=5), dict(dt=0.0), dict(hit_cap=16), dict(ztiles=True, tile_w=5, tile_h=5)):
         with pytest.raises(rgx.RgxError) as e:
             sc.forward(cb, rgx.make_opts(opts_with(w.options, **bad)))
         assert e.value.code == rgx.RGX_ERR_INVALID_ARG
