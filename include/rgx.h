@@ -83,7 +83,7 @@ typedef struct {
     float sigma_eps;             /* truncation density: support is sigma(x) >= sigma_eps */
     float bg[3];                 /* background colour, added as T_final * bg */
     int32_t tile_w, tile_h;      /* ray tile, tile_w * tile_h == 32 (ZTILES only) */
-    int32_t hit_cap;             /* chord-list capacity per ray (32..512); never drops hits */
+    int32_t hit_cap;             /* chord-list capacity per ray (multiple of 32, 32..512); never drops hits */
     int32_t max_segments;        /* loop bound per ray; 0 = derived from the ray length */
 } rgx_opts;
 

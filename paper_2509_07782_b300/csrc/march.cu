@@ -40,7 +40,7 @@
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
 #define WARPS (RGX_BLOCK / 32)
 #define STK 256                                     // per-warp traversal stack
-#define CANDS 64                                    // leaf candidates per traversal step
+#define CANDS 128                                   // pending leaf candidates (< 32 left + 64 new)
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -90,10 +90,11 @@ struct WS {
     uint32_t* stk;  // [STK] node refs
     float* stkt;    // [STK] entry distance (nearest-hit traversal)
     uint32_t* cand; // [CANDS]
+    float* Y;       // [16] SH basis of the current ray direction
 };
 
 __host__ __device__ inline size_t warp_bytes(int cap, bool bwd) {
-    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + CANDS * 4;
+    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + CANDS * 4 + 16 * 4;
     if (bwd) b += (size_t)cap * (16 + 8) + 32 * 16;
     return (b + 15) & ~(size_t)15;
 }
@@ -111,7 +112,8 @@ __device__ inline WS carve(char* base, int cap, bool bwd) {
     w.pid = (uint32_t*)p; p += (size_t)cap * 4;
     w.seg = (uint32_t*)p; p += (size_t)cap * 4;
     w.stk = (uint32_t*)p; p += (size_t)STK * 4;
-    w.cand = (uint32_t*)p;
+    w.cand = (uint32_t*)p; p += CANDS * 4;
+    w.Y = (float*)p;
     return w;
 }
 
@@ -178,21 +180,19 @@ __device__ __forceinline__ void local_frame(const float4* __restrict__ geom, int
     yc[2] = g3.x * ex + g3.y * ey + g3.z * ez + tc * yd[2];
 }
 
-// SH colour c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_k).
-__device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_t p, const float Y[16], float c[3]) {
+// SH colour c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_k); Y in shared memory.
+__device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_t p, const float* Y, float c[3]) {
     const float4* s = shc + 12 * p;
     float r = 0.5f, g = 0.5f, b = 0.5f;
 #pragma unroll
-    for (int j = 0; j < 12; j++) {
-        const float4 v = __ldg(&s[j]);
-        const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int idx = 4 * j + e;
-            const int k = idx / 3, ch = idx % 3;
-            const float t = Y[k] * vv[e];
-            if (ch == 0) r += t; else if (ch == 1) g += t; else b += t;
-        }
+    for (int j = 0; j < 4; j++) {
+        // coefficients 12j .. 12j+11 = SH indices 4j .. 4j+3, three channels each
+        const float4 v0 = __ldg(&s[3 * j]), v1 = __ldg(&s[3 * j + 1]), v2 = __ldg(&s[3 * j + 2]);
+        const float4 y = *reinterpret_cast<const float4*>(Y + 4 * j);
+        r += y.x * v0.x; g += y.x * v0.y; b += y.x * v0.z;
+        r += y.y * v0.w; g += y.y * v1.x; b += y.y * v1.y;
+        r += y.z * v1.z; g += y.z * v1.w; b += y.z * v2.x;
+        r += y.w * v2.y; g += y.w * v2.z; b += y.w * v2.w;
     }
     c[0] = fmaxf(r, 0.0f); c[1] = fmaxf(g, 0.0f); c[2] = fmaxf(b, 0.0f);
 }
@@ -211,61 +211,78 @@ struct NoChunk {
 };
 
 // Collect into the list every Gaussian whose exact chord overlaps [ta, tb).
-// Returns 0 when complete, 1 when the list would overflow (window mode: the
-// caller shrinks the window), 2 on a traversal-stack overflow.  In chunked
-// mode a full list is handed to `on_full(m)` and reset instead.
+// Traversal steps pop up to 32 nodes; leaf candidates are queued and their
+// chords solved in full 32-lane rounds; SH colours are computed afterwards for
+// the kept (compacted) entries only.  Returns 0 when complete, 1 when the list
+// would overflow (window mode: the caller shrinks the window), 2 on a
+// traversal-stack overflow.  In chunked mode a full list is handed to
+// `on_full(m)` and reset instead.
+__device__ __forceinline__ void colour_entries(const MarchParams& P, const WS& W, int from, int to) {
+    const int lane = threadIdx.x & 31;
+    for (int e = from + lane; e < to; e += 32) {
+        float col[3];
+        sh_colour(P.shc, W.pid[e], W.Y, col);
+        W.c[e] = make_float4(W.c[e].x, col[0], col[1], col[2]);
+    }
+    __syncwarp();
+}
+
 template <bool BWD, class OnFull>
-__device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, const float Y[16], float ta, float tb,
-                         int cap, int& nL, bool chunked, OnFull on_full, Counters& cnt) {
+__device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float ta, float tb, int cap, int& nL,
+                         bool chunked, OnFull on_full, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     if (lane == 0) W.stk[0] = 0u;
     __syncwarp();
-    int sp = 1;
-    while (sp > 0) {
-        const int room = (STK - sp) / 2;
-        const int take = min(min(sp, 32), room);
-        if (take <= 0) {
-            if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
-            return 2;
+    int sp = 1, npend = 0, ncol = nL;  // entries [ncol, nL) still need their colour
+    while (sp > 0 || npend > 0) {
+        if (sp > 0) {
+            const int room = (STK - sp) / 2;
+            const int take = min(min(sp, 32), room);
+            if (take <= 0) {
+                if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
+                return 2;
+            }
+            const int base = sp - take;
+            const uint32_t ref = lane < take ? W.stk[base + lane] : 0u;
+            __syncwarp();
+            sp = base;
+            bool hl_ = false, hr_ = false;
+            uint32_t rl = 0, rr = 0;
+            if (lane < take) {
+                cnt.visits++;
+                const float4* nd = P.nodes + 4 * (size_t)ref;
+                const float4 a0 = __ldg(nd), a1 = __ldg(nd + 1), a2 = __ldg(nd + 2), a3 = __ldg(nd + 3);
+                const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
+                float te;
+                hl_ = box_overlap(a0, a1, r, ta, tb, te);
+                hr_ = box_overlap(a2, a3, r, ta, tb, te);
+                rl = (first == split) ? (split | LEAF_BIT) : split;
+                rr = (split + 1 == last) ? ((split + 1) | LEAF_BIT) : (split + 1);
+            }
+            const bool pl = hl_ && !(rl & LEAF_BIT), pr = hr_ && !(rr & LEAF_BIT);
+            const bool ll = hl_ && (rl & LEAF_BIT), lr = hr_ && (rr & LEAF_BIT);
+            const uint32_t bpl = __ballot_sync(FULLMASK, pl), bpr = __ballot_sync(FULLMASK, pr);
+            const uint32_t bll = __ballot_sync(FULLMASK, ll), blr = __ballot_sync(FULLMASK, lr);
+            const int po = sp + __popc(bpl & lt) + __popc(bpr & lt);
+            if (pr) W.stk[po] = rr;
+            if (pl) W.stk[po + (pr ? 1 : 0)] = rl;
+            const int co = npend + __popc(bll & lt) + __popc(blr & lt);
+            if (ll) W.cand[co] = rl & ~LEAF_BIT;
+            if (lr) W.cand[co + (ll ? 1 : 0)] = rr & ~LEAF_BIT;
+            sp += __popc(bpl) + __popc(bpr);
+            npend += __popc(bll) + __popc(blr);
+            __syncwarp();
         }
-        const int base = sp - take;
-        const uint32_t ref = lane < take ? W.stk[base + lane] : 0u;
-        __syncwarp();
-        sp = base;
-        bool hl_ = false, hr_ = false;
-        uint32_t rl = 0, rr = 0;
-        if (lane < take) {
-            cnt.visits++;
-            const float4* nd = P.nodes + 4 * (size_t)ref;
-            const float4 a0 = __ldg(nd), a1 = __ldg(nd + 1), a2 = __ldg(nd + 2), a3 = __ldg(nd + 3);
-            const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
-            float te;
-            hl_ = box_overlap(a0, a1, r, ta, tb, te);
-            hr_ = box_overlap(a2, a3, r, ta, tb, te);
-            rl = (first == split) ? (split | LEAF_BIT) : split;
-            rr = (split + 1 == last) ? ((split + 1) | LEAF_BIT) : (split + 1);
-        }
-        const bool pl = hl_ && !(rl & LEAF_BIT), pr = hr_ && !(rr & LEAF_BIT);
-        const bool ll = hl_ && (rl & LEAF_BIT), lr = hr_ && (rr & LEAF_BIT);
-        const uint32_t bpl = __ballot_sync(FULLMASK, pl), bpr = __ballot_sync(FULLMASK, pr);
-        const uint32_t bll = __ballot_sync(FULLMASK, ll), blr = __ballot_sync(FULLMASK, lr);
-        const int po = sp + __popc(bpl & lt) + __popc(bpr & lt);
-        if (pr) W.stk[po] = rr;
-        if (pl) W.stk[po + (pr ? 1 : 0)] = rl;
-        const int co = __popc(bll & lt) + __popc(blr & lt);
-        if (ll) W.cand[co] = rl & ~LEAF_BIT;
-        if (lr) W.cand[co + (ll ? 1 : 0)] = rr & ~LEAF_BIT;
-        sp += __popc(bpl) + __popc(bpr);
-        const int nc = __popc(bll) + __popc(blr);
-        __syncwarp();
-        for (int c0 = 0; c0 < nc; c0 += 32) {
-            const bool have = c0 + lane < nc;
+        // solve queued candidates in full rounds (or everything once the stack is empty)
+        int done = 0;
+        while (npend - done >= 32 || (sp == 0 && npend - done > 0)) {
+            const bool have = done + lane < npend;
             Chord ch;
             ch.ok = false;
             int64_t p = 0;
             if (have) {
-                const uint32_t leaf = W.cand[c0 + lane];
+                const uint32_t leaf = W.cand[done + lane];
                 p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
                 ch = chord_of(P.geom, p, r);
             }
@@ -274,15 +291,15 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, const 
             const int nk = __popc(bk);
             if (nL + nk > cap) {
                 if (!chunked) return 1;
+                colour_entries(P, W, ncol, nL);
                 on_full(nL);
                 nL = 0;
+                ncol = 0;
             }
             if (keep) {
                 const int slot = nL + __popc(bk & lt);
-                float col[3];
-                sh_colour(P.shc, p, Y, col);
                 W.q[slot] = make_float4(ch.tc, ch.a, ch.qmin, ch.Qe);
-                W.c[slot] = make_float4(ch.L, col[0], col[1], col[2]);
+                W.c[slot] = make_float4(ch.L, 0.f, 0.f, 0.f);
                 W.tio[slot] = make_float2(ch.tin, ch.tout);
                 W.pid[slot] = (uint32_t)p;
                 if (BWD) {
@@ -291,9 +308,20 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, const 
                 }
             }
             nL += nk;
+            done = min(done + 32, npend);
+            __syncwarp();
+        }
+        if (done > 0) {
+            // move the (< 32) leftover candidates to the front
+            const int left = npend - done;
+            const uint32_t v = lane < left ? W.cand[done + lane] : 0u;
+            __syncwarp();
+            if (lane < left) W.cand[lane] = v;
+            npend = left;
             __syncwarp();
         }
     }
+    colour_entries(P, W, ncol, nL);
     return 0;
 }
 
@@ -429,7 +457,8 @@ __device__ __forceinline__ void red_add4(float4* addr, float a, float b, float c
 
 // Turn the accumulated per-(ray, Gaussian) sums of entries 0..m-1 into the
 // local-frame moments and add them (and the SH gradients) to the Gaussians.
-__device__ void flush_entries(const MarchParams& P, const WS& W, const Ray& r, const float Y[16], int m) {
+__device__ void flush_entries(const MarchParams& P, const WS& W, const Ray& r, int m) {
+    const float* Y = W.Y;
     const int lane = threadIdx.x & 31;
     for (int e = lane; e < m; e += 32) {
         const float4 a = W.acc[e];
@@ -512,8 +541,16 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         const float texit = fminf(fminf((fx - r.ox) * r.ix, (fy - r.oy) * r.iy), (fz - r.oz) * r.iz);
         tf = (in && texit > tn) ? texit : tn;
     }
-    float Y[16];
-    sh_basis16(r.dx, r.dy, r.dz, Y);
+    {
+        float Y[16];
+        sh_basis16(r.dx, r.dy, r.dz, Y);
+        __syncwarp();
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; i++) W.Y[i] = Y[i];
+        }
+        __syncwarp();
+    }
 
     const bool skip = (P.flags & RGX_SKIP) != 0;
     const bool uniform = (P.flags & RGX_ADAPTIVE) == 0;
@@ -556,7 +593,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         // ---- window of chords covering [tS, tcut)
         bool chunked = false;
         if (!(tS >= w_lo && tcut <= w_hi)) {
-            if (BWD) flush_entries(P, W, r, Y, nL);
+            if (BWD) flush_entries(P, W, r, nL);
             const float need = te - tS;
             float len = fmaxf(wlen, need);
             while (true) {
@@ -564,7 +601,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 hi = fmaxf(hi, tcut);
                 nL = 0;
                 if (lane == 0) cnt.windows++;
-                const int rc = w_collect<BWD>(P, W, r, Y, tS, hi, cap, nL, false, NoChunk(), cnt);
+                const int rc = w_collect<BWD>(P, W, r, tS, hi, cap, nL, false, NoChunk(), cnt);
                 if (rc == 0) {
                     w_lo = tS; w_hi = hi;
                     wlen = (nL * 4 <= cap) ? 2.0f * len : len;
@@ -599,7 +636,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 __syncwarp();
             };
             nL = 0;
-            w_collect<BWD>(P, W, r, Y, tS, tcut, cap, nL, true, onfull, cnt);
+            w_collect<BWD>(P, W, r, tS, tcut, cap, nL, true, onfull, cnt);
             if (nL) onfull(nL);
             nexact = tot;
             nL = 0;
@@ -698,10 +735,10 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 auto onfull2 = [&](int m) {
                     adjoint_entries<NS>(W, false, m, tS, dtk);
                     __syncwarp();
-                    flush_entries(P, W, r, Y, m);
+                    flush_entries(P, W, r, m);
                 };
                 nL = 0;
-                w_collect<BWD>(P, W, r, Y, tS, tcut, cap, nL, true, onfull2, cnt);
+                w_collect<BWD>(P, W, r, tS, tcut, cap, nL, true, onfull2, cnt);
                 if (nL) onfull2(nL);
                 nL = 0;
             }
@@ -713,7 +750,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         if (uniform) { j += NS; tS = __fmaf_rn((float)j, P.dt, tn); } else tS = te;
     }
     if (BWD) {
-        flush_entries(P, W, r, Y, nL);
+        flush_entries(P, W, r, nL);
         if (lane == 0 && T != Tf) atomicOr(P.status, (unsigned)RGX_ERR_REPLAY);
     } else {
         o_rgba = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
@@ -895,7 +932,8 @@ static rgx_status check_opts(rgx_scene* s, const rgx_opts* o) {
     } else if (!(o->dt > 0.0f)) {
         return set_err(s, RGX_ERR_INVALID_ARG, "dt must be > 0");
     }
-    if (o->hit_cap < 32 || o->hit_cap > 512) return set_err(s, RGX_ERR_INVALID_ARG, "hit_cap must be in [32, 512]");
+    if (o->hit_cap < 32 || o->hit_cap > 512 || (o->hit_cap & 31))
+        return set_err(s, RGX_ERR_INVALID_ARG, "hit_cap must be a multiple of 32 in [32, 512]");
     if ((o->flags & RGX_ZTILES) && (o->tile_w <= 0 || o->tile_h <= 0 || o->tile_w * o->tile_h != 32))
         return set_err(s, RGX_ERR_INVALID_ARG, "tile_w * tile_h must be 32");
     if (!(o->t_eps >= 0.0f)) return set_err(s, RGX_ERR_INVALID_ARG, "t_eps must be >= 0");

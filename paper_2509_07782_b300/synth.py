@@ -95,7 +95,7 @@ class Options:
     bg: tuple = (0.0, 0.0, 0.0)
     tile_w: int = 8
     tile_h: int = 4
-    hit_cap: int = 128
+    hit_cap: int = 256
     max_segments: int = 0       # 0 = derived from the ray length
 
 
