@@ -206,6 +206,28 @@ rgx_status rgx_get_bvh(rgx_scene* scene, uint64_t* codes, int32_t* perm, float* 
  */
 rgx_status rgx_get_counters(rgx_scene* scene, uint64_t* out8, void* stream);
 
+/*
+ * Allocation-free Morton sort: the Z-order codes and permutation that
+ * rgx_build_bvh computes (scene bounds of the means, 30-bit or, with
+ * wide != 0, 63-bit codes, stable radix sort of (code, index)), written to
+ * codes [n] (uint64, ascending) and perm [n] (int32, sorted position -> input
+ * index).  The paper has no counterpart to this entry point; it exists for
+ * callers that cannot call cudaMalloc: code that runs while a CUDA graph is
+ * being captured, plugins living inside another engine whose allocator owns
+ * all device memory, and real-time loops that must not allocate.  It
+ * allocates nothing: its scratch is a fixed static device array of about
+ * 6.3 MB that every GPU loading the library keeps until the process exits.
+ *   - n must be at most 262144; larger n returns RGX_ERR_INVALID_ARG.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the one array: calls that overlap on the GPU (other
+ *     streams, other threads) race and must be serialised by the caller.
+ *   - means, codes and perm are device pointers on the current device;
+ *     the work is enqueued on `stream`.
+ */
+rgx_status rgx_morton_sort_noalloc(int64_t n, const float* means, int32_t wide, uint64_t* codes,
+                                   int32_t* perm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

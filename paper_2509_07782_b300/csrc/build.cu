@@ -419,3 +419,92 @@ extern "C" rgx_status rgx_build_bvh(rgx_scene* s, int64_t n, int32_t sh_degree, 
     RGX_CUDA(s, cudaGetLastError());
     return RGX_OK;
 }
+
+// ------------------------------------------------------------------ allocation-free variant
+// rgx_morton_sort_noalloc runs the same bounds -> Morton code -> radix sort
+// pipeline as rgx_build_bvh, but its scratch (two key/value ping-pong buffers,
+// the digit histogram and the bounds) lives in the file-scope array below
+// instead of a scene workspace, so the call allocates nothing.  The array is
+// RGX_NOALLOC_BYTES (about 6.3 MB) on every GPU that loads the library, for
+// the life of the process.
+#define RGX_NOALLOC_MAX_N (1 << 18)
+#define RGX_NOALLOC_NB ((RGX_NOALLOC_MAX_N + RS_TILE - 1) / RS_TILE)
+#define RGX_NOALLOC_BYTES ((size_t)RGX_NOALLOC_MAX_N * (2 * 8 + 2 * 4) + (size_t)256 * RGX_NOALLOC_NB * 4 + 256)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RGX_NOALLOC_BYTES];
+
+#define RGX_MAX_DEVICES 64
+static void* g_noalloc_addr[RGX_MAX_DEVICES];
+
+// per-axis min/max of the means only (no other parameter is read here)
+__global__ void k_bounds_means(int64_t n, const float* __restrict__ means, unsigned int* __restrict__ bounds) {
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; a++) {
+            const float m = means[3 * l + a];
+            lo[a] = fminf(lo[a], m);
+            hi[a] = fmaxf(hi[a], m);
+        }
+    }
+    for (int a = 0; a < 3; a++) {
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(FULLMASK, lo[a], off));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(FULLMASK, hi[a], off));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int a = 0; a < 3; a++) {
+            atomicMin(&bounds[a], f2ord(lo[a]));
+            atomicMax(&bounds[3 + a], f2ord(hi[a]));
+        }
+    }
+}
+
+extern "C" rgx_status rgx_morton_sort_noalloc(int64_t n, const float* means, int32_t wide, uint64_t* codes,
+                                              int32_t* perm, void* stream_) {
+    if (n < 0 || n > RGX_NOALLOC_MAX_N)
+        return set_err(nullptr, RGX_ERR_INVALID_ARG,
+                       "rgx_morton_sort_noalloc: n must be in [0, 262144] (the size of its static scratch)");
+    if (n > 0 && (!means || !codes || !perm))
+        return set_err(nullptr, RGX_ERR_INVALID_ARG, "rgx_morton_sort_noalloc: null pointer");
+    if (n == 0) return RGX_OK;
+    int dev = 0;
+    RGX_CUDA(nullptr, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= RGX_MAX_DEVICES)
+        return set_err(nullptr, RGX_ERR_INVALID_ARG, "rgx_morton_sort_noalloc: device index too large");
+    if (!g_noalloc_addr[dev]) {
+        // first call on this device: the host-side name of the array is not a
+        // device address; ask the runtime for it (with this device current)
+        void* p = nullptr;
+        RGX_CUDA(nullptr, cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    unsigned char* base = (unsigned char*)g_noalloc_addr[dev];
+    uint64_t* keys[2] = {(uint64_t*)base, (uint64_t*)base + RGX_NOALLOC_MAX_N};
+    uint32_t* vals0 = (uint32_t*)(base + (size_t)RGX_NOALLOC_MAX_N * 16);
+    uint32_t* vals[2] = {vals0, vals0 + RGX_NOALLOC_MAX_N};
+    uint32_t* hist = vals0 + 2 * (size_t)RGX_NOALLOC_MAX_N;
+    unsigned int* bounds = (unsigned int*)(hist + (size_t)256 * RGX_NOALLOC_NB);
+    cudaStream_t st = (cudaStream_t)stream_;
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int T = 256;
+    const int g = grid_for(n, T, nsm);
+    // the array keeps the previous call's contents: the bounds must restart
+    RGX_CUDA(nullptr, cudaMemsetAsync(bounds, 0xff, 3 * sizeof(unsigned), st));
+    RGX_CUDA(nullptr, cudaMemsetAsync(bounds + 3, 0x00, 3 * sizeof(unsigned), st));
+    k_bounds_means<<<g, T, 0, st>>>(n, means, bounds);
+    k_morton<<<g, T, 0, st>>>(n, means, bounds, wide ? 1 : 0, keys[0], vals[0]);
+    const int passes = wide ? 8 : 4;
+    const int nb = (int)((n + RS_TILE - 1) / RS_TILE);
+    int cur = 0;
+    for (int p = 0; p < passes; p++) {
+        k_rs_hist<<<nb, RS_THREADS, 0, st>>>(keys[cur], n, 8 * p, hist, nb);
+        k_rs_scan<<<1, 1024, 0, st>>>(hist, 256 * nb);
+        k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, 8 * p, hist, nb);
+        cur ^= 1;
+    }
+    RGX_CUDA(nullptr, cudaMemcpyAsync(codes, keys[cur], (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+    RGX_CUDA(nullptr, cudaMemcpyAsync(perm, vals[cur], (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    RGX_CUDA(nullptr, cudaGetLastError());
+    return RGX_OK;
+}

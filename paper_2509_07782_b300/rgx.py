@@ -35,7 +35,8 @@ RGX_SKIP, RGX_ADAPTIVE, RGX_MORTON, RGX_ZTILES, RGX_MORTON63 = 1, 2, 4, 8, 16
 
 EXPORTS = ["rgx_scene_create", "rgx_scene_destroy", "rgx_build_bvh", "rgx_render_forward",
            "rgx_render_forward_sched", "rgx_render_backward", "rgx_sync_status", "rgx_fwd_state_bytes",
-           "rgx_last_error", "rgx_get_bvh", "rgx_get_counters", "rgx_autotune"]
+           "rgx_last_error", "rgx_get_bvh", "rgx_get_counters", "rgx_autotune",
+           "rgx_morton_sort_noalloc"]
 
 
 class RgxCamera(C.Structure):
@@ -85,6 +86,7 @@ def lib() -> C.CDLL:
             l.rgx_last_error.argtypes = [vp]
             l.rgx_get_bvh.argtypes = [vp, vp, vp, vp, vp, vp]
             l.rgx_get_counters.argtypes = [vp, C.POINTER(C.c_uint64), vp]
+            l.rgx_morton_sort_noalloc.argtypes = [i64, fp, C.c_int32, vp, vp, vp]
             l.rgx_autotune.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), C.c_int32,
                                        C.c_int32, fp, vp, fp, fp, fp, fp, fp, fp, C.POINTER(RgxOpts),
                                        C.POINTER(C.c_float), vp]
@@ -221,6 +223,14 @@ def rgx_autotune(h, cams: Cameras, base, tune_ns, with_backward, rgba, state, d_
                               _ptr(rgba), _ptr(state), _ptr(d_rgba), *[_ptr(x) for x in g], C.byref(best),
                               C.byref(ms), _stream(stream)), h)
     return best, float(ms.value)
+
+
+def rgx_morton_sort_noalloc(means, wide, codes, perm, stream=None):
+    """Sorted Morton codes / permutation of `means` with no device allocation
+    (static scratch, n <= 262144).  codes: int64 [n] (uint64 bits), perm: int32 [n]."""
+    n = int(means.shape[0])
+    _check(lib().rgx_morton_sort_noalloc(n, _ptr(means), int(bool(wide)), _ptr(codes), _ptr(perm),
+                                         _stream(stream)))
 
 
 # ------------------------------------------------------------------ convenience
