@@ -45,6 +45,7 @@
 struct MarchParams {
     const float4* __restrict__ geom;
     const float4* __restrict__ shc;
+    const float4* __restrict__ sph;
     const int32_t* __restrict__ perm;
     const float4* __restrict__ nodes;
     const float* __restrict__ root;
@@ -89,12 +90,13 @@ struct WS {
     uint32_t* seg;  // [cap] entries of the current segment
     uint32_t* stk;  // [STK] node refs
     float* stkt;    // [STK] entry distance (nearest-hit traversal)
-    uint32_t* cand; // [CANDS]
+    uint32_t* cand; // [CANDS] leaf candidates awaiting the sphere test
+    uint32_t* surv; // [CANDS] sphere survivors awaiting the exact chord
     float* Y;       // [16] SH basis of the current ray direction
 };
 
 __host__ __device__ inline size_t warp_bytes(int cap, bool bwd) {
-    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + CANDS * 4 + 16 * 4;
+    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + 2 * CANDS * 4 + 16 * 4;
     if (bwd) b += (size_t)cap * (16 + 8) + 32 * 16;
     return (b + 15) & ~(size_t)15;
 }
@@ -113,6 +115,7 @@ __device__ inline WS carve(char* base, int cap, bool bwd) {
     w.seg = (uint32_t*)p; p += (size_t)cap * 4;
     w.stk = (uint32_t*)p; p += (size_t)STK * 4;
     w.cand = (uint32_t*)p; p += CANDS * 4;
+    w.surv = (uint32_t*)p; p += CANDS * 4;
     w.Y = (float*)p;
     return w;
 }
@@ -234,11 +237,12 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
     const uint32_t lt = lanemask_lt();
     if (lane == 0) W.stk[0] = 0u;
     __syncwarp();
-    int sp = 1, npend = 0, ncol = nL;  // entries [ncol, nL) still need their colour
-    while (sp > 0 || npend > 0) {
+    int sp = 1, npend = 0, nsurv = 0, ncol = nL;  // entries [ncol, nL) still need their colour
+    while (sp > 0 || npend > 0 || nsurv > 0) {
         if (sp > 0) {
-            const int room = (STK - sp) / 2;
-            const int take = min(min(sp, 32), room);
+            // wide pops while the stack has room, then depth-first with a reserve
+            // (100 entries > the depth bound of the radix tree)
+            const int take = STK - sp >= 2 ? min(min(sp, 32), max((STK - 100 - sp) / 2, 1)) : 0;
             if (take <= 0) {
                 if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
                 return 2;
@@ -274,19 +278,51 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
             npend += __popc(bll) + __popc(blr);
             __syncwarp();
         }
-        // solve queued candidates in full rounds (or everything once the stack is empty)
+        // bounding-sphere test of queued candidates in full rounds (everything once
+        // the stack is empty); survivors are queued for the exact chord
         int done = 0;
         while (npend - done >= 32 || (sp == 0 && npend - done > 0)) {
             const bool have = done + lane < npend;
-            Chord ch;
-            ch.ok = false;
-            int64_t p = 0;
+            uint32_t p = 0;
+            bool maybe = false;
             if (have) {
                 const uint32_t leaf = W.cand[done + lane];
-                p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
-                ch = chord_of(P.geom, p, r);
+                p = P.morton ? leaf : (uint32_t)P.perm[leaf];
+                const float4 sp4 = __ldg(&P.sph[p]);
+                const float vx = sp4.x - r.ox, vy = sp4.y - r.oy, vz = sp4.z - r.oz;
+                const float tp = vx * r.dx + vy * r.dy + vz * r.dz;
+                const float vv = vx * vx + vy * vy + vz * vz;
+                maybe = sp4.w > 0.0f && vv - tp * tp <= sp4.w * sp4.w + 4e-6f * vv && tp + sp4.w > ta &&
+                        tp - sp4.w < tb;
             }
-            const bool keep = have && ch.ok && ch.tout > ta && ch.tin < tb;
+            const uint32_t bm = __ballot_sync(FULLMASK, maybe);
+            if (maybe) W.surv[nsurv + __popc(bm & lt)] = p;
+            nsurv += __popc(bm);
+            done = min(done + 32, npend);
+            __syncwarp();
+        }
+        if (done > 0) {
+            // move the (< 32) leftover candidates to the front
+            const int left = npend - done;
+            const uint32_t v = lane < left ? W.cand[done + lane] : 0u;
+            __syncwarp();
+            if (lane < left) W.cand[lane] = v;
+            npend = left;
+            __syncwarp();
+        }
+        // exact chords of the sphere survivors, 32 at a time (all of them once
+        // the traversal has finished)
+        while (nsurv >= 32 || (sp == 0 && nsurv > 0)) {
+            const int m = min(nsurv, 32);
+            const bool h2 = lane < m;
+            Chord ch;
+            ch.ok = false;
+            uint32_t q = 0;
+            if (h2) {
+                q = W.surv[nsurv - m + lane];
+                ch = chord_of(P.geom, q, r);
+            }
+            const bool keep = h2 && ch.ok && ch.tout > ta && ch.tin < tb;
             const uint32_t bk = __ballot_sync(FULLMASK, keep);
             const int nk = __popc(bk);
             if (nL + nk > cap) {
@@ -301,23 +337,14 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
                 W.q[slot] = make_float4(ch.tc, ch.a, ch.qmin, ch.Qe);
                 W.c[slot] = make_float4(ch.L, 0.f, 0.f, 0.f);
                 W.tio[slot] = make_float2(ch.tin, ch.tout);
-                W.pid[slot] = (uint32_t)p;
+                W.pid[slot] = q;
                 if (BWD) {
                     W.acc[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
                     W.acc2[slot] = make_float2(0.f, 0.f);
                 }
             }
             nL += nk;
-            done = min(done + 32, npend);
-            __syncwarp();
-        }
-        if (done > 0) {
-            // move the (< 32) leftover candidates to the front
-            const int left = npend - done;
-            const uint32_t v = lane < left ? W.cand[done + lane] : 0u;
-            __syncwarp();
-            if (lane < left) W.cand[lane] = v;
-            npend = left;
+            nsurv -= m;
             __syncwarp();
         }
     }
@@ -336,8 +363,7 @@ __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, floa
     int sp = 1;
     float best = tf;
     while (sp > 0) {
-        const int room = (STK - sp) / 2;
-        const int take = min(min(sp, 32), room);
+        const int take = STK - sp >= 2 ? min(min(sp, 32), max((STK - 100 - sp) / 2, 1)) : 0;
         if (take <= 0) {
             if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
             return best;
@@ -959,7 +985,7 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
                                int32_t* sched_n, cudaStream_t st) {
     MarchParams P;
     memset(&P, 0, sizeof P);
-    P.geom = s->geom; P.shc = s->shc; P.perm = s->perm; P.nodes = s->nodes; P.root = s->root;
+    P.geom = s->geom; P.shc = s->shc; P.sph = s->sph; P.perm = s->perm; P.nodes = s->nodes; P.root = s->root;
     P.n = s->n; P.morton = s->morton;
     P.cams = s->cams; P.ncam = ncam;
     P.flags = o->flags;
