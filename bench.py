@@ -113,6 +113,22 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_2509_07782_b300", "csrc", "march.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 5 and parts[0] == "traffic_bytes_per_launch" and parts[1] == kernel:
+                if parts[4] == sha:
+                    return int(parts[2])
+    return None
+
+
 def launches_per_step(opts) -> int:
     passes = 8 if opts.morton63 else 4
     build = 2 + 3 * passes + 1 + 2       # bounds, morton, sort passes, pack, karras + refit
@@ -382,9 +398,10 @@ def main():
     fwd_s = r["fwd_ms"] / 1e3
     dominant_is_bwd = r["bwd_ms"] >= r["fwd_ms"]
     achieved = (flops_b / bwd_s if dominant_is_bwd else flops_f / fwd_s) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_march<16,bwd>" if dominant_is_bwd else "k_march<16,fwd>",
+    kname = "k_march<16,1>" if dominant_is_bwd else "k_march<16,0>"
+    roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": None,
+                "traffic": profiled_traffic(kname),
                 "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived), HBM {src} "
                                f"{peaks.get('hbm_gbs')} GB/s"}
     out = {
