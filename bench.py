@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--impl", default="rgx", choices=["rgx", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_1m", "sweep_6m"],
+                   help="extra measurements: batch_1m = 8 uneven views, autotuned, CUDA-graph captured "
+                        "fwd+bwd; sweep_6m = 64 views forward, one persistent launch vs one launch per view")
     return p.parse_args()
 
 
@@ -340,9 +343,113 @@ def cpu_baseline(max_seconds=12.0, npix_start=256):
             "sample": f"{len(pix)} seeded pixels of the 800x800 view, forward + adjoint, {dt:.2f} s"}
 
 
+def run_batch(args):
+    """batch_1m: 1M Gaussians, 8 views of uneven resolution, one persistent
+    forward + adjoint launch each, tuned by rgx_autotune, captured in a CUDA graph."""
+    import torch
+
+    from paper_2509_07782_b300 import graph, rgx, synth
+    dev = torch.device("cuda", 0)
+    w = synth.workload("batch_1m")
+    base = rgx.make_opts(w.options)
+    cams = rgx.Cameras(w.cameras)
+    params = list(rgx.scene_tensors(w.scene, device=dev))
+    sc = rgx.Scene(0)
+    sc.build(*params, base)
+    best, tune_ms = sc.autotune(cams, base, tune_ns=False, with_backward=True)
+    d_rgba = torch.randn(cams.n_rays, 4, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for name, opts in (("autotuned", best), ("default", base)):
+        step = graph.CapturedStep(sc, cams, opts, params, d_rgba)
+        for _ in range(max(args.warmup, 3)):
+            step.replay()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(step.stream)
+            step.replay()
+            e1.record(step.stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            flush.fill_(0.0)
+        out[name] = statistics.median(times)
+        if sc.status(step.stream) != 0:
+            out[name + "_status"] = "device status nonzero"
+    ms = out["autotuned"]
+    return {"metric": METRIC, "value": cams.n_rays / ms / 1e3, "unit": "Mrays/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch_1m: 1M torus Gaussians, 8 views {320x240 ... 1920x1080}, "
+                                   "BVH rebuild + persistent forward + adjoint, CUDA-graph captured",
+                       "rays_per_step": cams.n_rays, "l2": "flushed between steps"},
+            "autotuned": {"tile": [best.tile_w, best.tile_h], "hit_cap": best.hit_cap, "n_s": best.n_s,
+                          "tuning_ms": tune_ms},
+            "graph_ms_autotuned": out["autotuned"], "graph_ms_default": out["default"]}
+
+
+def run_sweep(args):
+    """sweep_6m: 6M Gaussians, 64 views, forward only: one persistent launch
+    for all views vs one launch per view; FPS per view size."""
+    import torch
+
+    from paper_2509_07782_b300 import rgx, synth
+    dev = torch.device("cuda", 0)
+    w = synth.workload("sweep_6m")
+    opts = rgx.make_opts(w.options)
+    t = rgx.scene_tensors(w.scene, device=dev)
+    sc = rgx.Scene(0)
+    sc.build(*t, opts)
+    cams_all = rgx.Cameras(w.cameras)
+    singles = [rgx.Cameras([c]) for c in w.cameras]
+    rgba = torch.empty(cams_all.n_rays, 4, device=dev)
+    st = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 1)):
+        rgx.rgx_render_forward(sc.h, cams_all, opts, rgba)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        rgx.rgx_render_forward(sc.h, cams_all, opts, rgba)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_persistent = e0.elapsed_time(e1) / args.steps
+    per_view = []
+    outs = [torch.empty(c.n_rays, 4, device=dev) for c in singles]
+    for c, o in zip(singles, outs):
+        rgx.rgx_render_forward(sc.h, c, opts, o)
+    torch.cuda.synchronize()
+    for c, o in zip(singles, outs):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        rgx.rgx_render_forward(sc.h, c, opts, o)
+        b.record(st)
+        torch.cuda.synchronize()
+        per_view.append((c.cams[0].width, c.cams[0].height, a.elapsed_time(b)))
+    ms_per_view_total = sum(x[2] for x in per_view)
+    fps = sorted(((wd * ht, 1e3 / ms) for wd, ht, ms in per_view))
+    q = [fps[0], fps[len(fps) // 2], fps[-1]]
+    return {"metric": METRIC, "value": cams_all.n_rays / ms_persistent / 1e3, "unit": "Mrays/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_persistent, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep_6m: 6M torus Gaussians, 64 seeded views 256..1920 x 256..1080, forward "
+                                   "only", "rays_per_step": cams_all.n_rays},
+            "one_launch_per_view": {"ms_total": ms_per_view_total,
+                                    "mrays_s": cams_all.n_rays / ms_per_view_total / 1e3},
+            "fps_per_view": {"smallest": {"pixels": q[0][0], "fps": q[0][1]},
+                             "median": {"pixels": q[1][0], "fps": q[1][1]},
+                             "largest": {"pixels": q[2][0], "fps": q[2][1]}},
+            "device_status": sc.status()}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload != WORKLOAD and args.impl != "reference":
+        if rank == 0:
+            print(json.dumps(run_batch(args) if args.workload == "batch_1m" else run_sweep(args)))
+        return
     if args.impl == "reference":
         if rank != 0:
             return
