@@ -174,6 +174,28 @@ rgx_status rgx_autotune(rgx_scene* scene, const rgx_camera* cams, int32_t ncam, 
                         const float* d_rgba, float* d_means, float* d_scales, float* d_quats,
                         float* d_densities, float* d_sh, rgx_opts* best, float* best_ms, void* stream);
 
+/*
+ * Isotropic loss, Sec. 3.4 Eqs. 6-8: L_s = 1/n sum_l max(r_max,l - r0, 0) with
+ * r_max = 2/(pi sqrt 3) (s1^2+s2^2+s3^2)^(3/2) / (s1 s2 s3), the rotation-free
+ * bound of a Gaussian's AABB/ellipsoid volume ratio (Supp. Sec. 2.3).
+ * Enqueues on `stream`: *loss += weight * L_s (one device float) and
+ * d_scales[n,3] += weight * dL_s/ds (linear scales, s > 0).  The paper uses
+ * r0 = 10 and weight lambda_s = 2.5e-4 (Sec. 4.2).
+ */
+rgx_status rgx_isotropic_loss(int64_t n, const float* scales, float r0, float weight, float* loss,
+                              float* d_scales, void* stream);
+
+/*
+ * Densification statistic, Sec. 3.5 Eq. 11, for one view: for every Gaussian
+ * whose mean gradient d_means[l] (from rgx_render_backward of this single
+ * view) is non-zero, stat[l] += |means[l] - o| / f * |d_means[l]| and
+ * count[l] += 1 (int32), with o the camera centre and f its focal length fx
+ * in pixels (HOST cam).  Densify where stat / count > tau (tau = 1.5e-4 in
+ * Sec. 4.2).  Enqueues on `stream`.
+ */
+rgx_status rgx_densify_accumulate(int64_t n, const float* means, const float* d_means,
+                                  const rgx_camera* cam, float* stat, int32_t* count, void* stream);
+
 /* Synchronise `stream`, return the device status word (RGX_ERR_* bits, 0 if
  * clean) and clear it. */
 rgx_status rgx_sync_status(rgx_scene* scene, void* stream);

@@ -36,7 +36,7 @@ RGX_SKIP, RGX_ADAPTIVE, RGX_MORTON, RGX_ZTILES, RGX_MORTON63 = 1, 2, 4, 8, 16
 EXPORTS = ["rgx_scene_create", "rgx_scene_destroy", "rgx_build_bvh", "rgx_render_forward",
            "rgx_render_forward_sched", "rgx_render_backward", "rgx_sync_status", "rgx_fwd_state_bytes",
            "rgx_last_error", "rgx_get_bvh", "rgx_get_counters", "rgx_autotune",
-           "rgx_morton_sort_noalloc"]
+           "rgx_morton_sort_noalloc", "rgx_isotropic_loss", "rgx_densify_accumulate"]
 
 
 class RgxCamera(C.Structure):
@@ -87,6 +87,8 @@ def lib() -> C.CDLL:
             l.rgx_get_bvh.argtypes = [vp, vp, vp, vp, vp, vp]
             l.rgx_get_counters.argtypes = [vp, C.POINTER(C.c_uint64), vp]
             l.rgx_morton_sort_noalloc.argtypes = [i64, fp, C.c_int32, vp, vp, vp]
+            l.rgx_isotropic_loss.argtypes = [i64, fp, C.c_float, C.c_float, fp, fp, vp]
+            l.rgx_densify_accumulate.argtypes = [i64, fp, fp, C.POINTER(RgxCamera), fp, vp, vp]
             l.rgx_autotune.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), C.c_int32,
                                        C.c_int32, fp, vp, fp, fp, fp, fp, fp, fp, C.POINTER(RgxOpts),
                                        C.POINTER(C.c_float), vp]
@@ -231,6 +233,20 @@ def rgx_morton_sort_noalloc(means, wide, codes, perm, stream=None):
     n = int(means.shape[0])
     _check(lib().rgx_morton_sort_noalloc(n, _ptr(means), int(bool(wide)), _ptr(codes), _ptr(perm),
                                          _stream(stream)))
+
+
+def rgx_isotropic_loss(scales, r0, weight, loss, d_scales, stream=None):
+    """loss (device float [1]) += weight * L_s; d_scales += weight * dL_s/ds (Eqs. 6-8)."""
+    _check(lib().rgx_isotropic_loss(int(scales.shape[0]), _ptr(scales), float(r0), float(weight), _ptr(loss),
+                                    _ptr(d_scales), _stream(stream)))
+
+
+def rgx_densify_accumulate(means, d_means, cams: Cameras, stat, count, stream=None):
+    """Eq. 11 statistic of one view (cams holds exactly one camera)."""
+    if cams.count != 1:
+        raise ValueError("one camera per call")
+    _check(lib().rgx_densify_accumulate(int(means.shape[0]), _ptr(means), _ptr(d_means), cams.ptr, _ptr(stat),
+                                        _ptr(count), _stream(stream)))
 
 
 # ------------------------------------------------------------------ convenience
