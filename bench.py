@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--impl", default="rgx", choices=["rgx", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-tune", action="store_true",
+                   help="skip rgx_autotune (tile shape and hit_cap; N_S fixed) before the timed steps")
     p.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_1m", "sweep_6m"],
                    help="extra measurements: batch_1m = 8 uneven views, autotuned, CUDA-graph captured "
                         "fwd+bwd; sweep_6m = 64 views forward, one persistent launch vs one launch per view")
@@ -185,6 +187,13 @@ def run_rgx(args, rank, world, local):
     upstream = torch.randn(R, 4, device=dev, generator=torch.Generator(device=dev).manual_seed(1 + rank))
     grads = [torch.zeros_like(x) for x in t]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tuned = None
+    if not args.no_tune:
+        # implementation knobs only (tile shape, hit-list capacity); N_S stays the workload's
+        sc.build(*t, opts)
+        best, tune_ms = sc.autotune(cams, opts, tune_ns=False, with_backward=True)
+        opts = best
+        tuned = {"tile": [best.tile_w, best.tile_h], "hit_cap": best.hit_cap, "tuning_ms": tune_ms}
 
     def step(ev=None):
         if ev is not None:
@@ -315,7 +324,7 @@ def run_rgx(args, rank, world, local):
                 fwd_ms=statistics.median(fwd_ms), bwd_ms=statistics.median(bwd_ms), wall_s=wall,
                 e2e=dict(value=world * R / (e2e_ms / 1e3) / 1e6, unit="Mrays/s", h2d_bytes_per_step=h2d,
                          d2h_bytes_per_step=d2h, ms_per_step=e2e_ms),
-                counters_fwd=cf, counters_bwd=cb, clocks=clocks, status=st, plain=plain, opts=w.options,
+                counters_fwd=cf, counters_bwd=cb, clocks=clocks, status=st, plain=plain, opts=w.options, tuned=tuned,
                 n=w.scene.n, steps_launches=launches_per_step(w.options) * args.steps)
 
 
@@ -516,9 +525,11 @@ def main():
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: {r['n']} Gaussians on a torus, one 800x800 view, BVH rebuild + "
-                               "forward + adjoint (skip + adaptive Eq.5 + Z-order + 8x4 Z-tiles, N_S=16)",
+                               "forward + adjoint (skip + adaptive Eq.5 + Z-order + Z-tiles, N_S=16; tile shape "
+                               "and hit_cap from rgx_autotune unless --no-tune)",
                    "rays_per_step_per_gpu": r["R"], "l2": "flushed (256 MiB write) between steps",
-                   "parallelism": f"{world} independent views, no data-path collective"},
+                   "parallelism": f"{world} independent views, no data-path collective",
+                   "autotuned": r["tuned"]},
         "fwd_bwd_ms": r["fwd_ms"] + r["bwd_ms"], "build_ms": r["build_ms"], "fwd_ms": r["fwd_ms"],
         "bwd_ms": r["bwd_ms"], "render_mrays_s": r["R"] / r["fwd_ms"] / 1e3,
         "plain_marcher": r["plain"],

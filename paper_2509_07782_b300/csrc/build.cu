@@ -14,6 +14,7 @@
 //               per internal node, ties broken by sorted position
 //   k_refit     bottom-up AABB union with per-node arrival counters
 #include <stdio.h>
+#include <cuda_fp16.h>
 #include "common.cuh"
 
 #define FULLMASK 0xffffffffu
@@ -324,6 +325,26 @@ __global__ void k_single(const float4* __restrict__ leafbox, float4* nodes, floa
     root[0] = lo.x; root[1] = lo.y; root[2] = lo.z; root[3] = hi.x; root[4] = hi.y; root[5] = hi.z;
 }
 
+// Half-precision copy of the refitted nodes for the traversals (outward rounding).
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+__global__ void k_compress(int64_t n_internal, const float4* __restrict__ nodes, uint4* __restrict__ nodeh) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_internal; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a0 = nodes[4 * i], a1 = nodes[4 * i + 1], a2 = nodes[4 * i + 2], a3 = nodes[4 * i + 3];
+        const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
+        const uint32_t rl = (first == split) ? (split | 0x80000000u) : split;
+        const uint32_t rr = (split + 1 == last) ? ((split + 1) | 0x80000000u) : (split + 1);
+        nodeh[2 * i] = make_uint4(pack_h2(__float2half_rd(a0.x), __float2half_rd(a0.y)),
+                                  pack_h2(__float2half_rd(a0.z), __float2half_ru(a1.x)),
+                                  pack_h2(__float2half_ru(a1.y), __float2half_ru(a1.z)), rl);
+        nodeh[2 * i + 1] = make_uint4(pack_h2(__float2half_rd(a2.x), __float2half_rd(a2.y)),
+                                      pack_h2(__float2half_rd(a2.z), __float2half_ru(a3.x)),
+                                      pack_h2(__float2half_ru(a3.y), __float2half_ru(a3.z)), rr);
+    }
+}
+
 __global__ void k_empty_root(float* root) {
     root[0] = root[1] = root[2] = INFINITY;
     root[3] = root[4] = root[5] = -INFINITY;
@@ -351,6 +372,7 @@ rgx_status rgx_internal_reserve(rgx_scene* s, int64_t n) {
     e = e ? e : grow(&s->keys[0], c); e = e ? e : grow(&s->keys[1], c);
     e = e ? e : grow(&s->vals[0], c); e = e ? e : grow(&s->vals[1], c);
     e = e ? e : grow(&s->nodes, 4 * (size_t)c);
+    e = e ? e : grow(&s->nodeh, 2 * (size_t)c);
     e = e ? e : grow(&s->parent, 2 * (size_t)c);
     e = e ? e : grow(&s->visit, (size_t)c);
     e = e ? e : grow(&s->geom, 4 * (size_t)c);
@@ -421,6 +443,8 @@ extern "C" rgx_status rgx_build_bvh(rgx_scene* s, int64_t n, int32_t sh_degree, 
         RGX_CUDA(s, cudaMemsetAsync(s->visit, 0, (size_t)(n - 1) * sizeof(int32_t), st));
         k_refit<<<g, T, 0, st>>>(n, s->leafbox, s->nodes, s->parent, s->visit, s->root);
     }
+    const int64_t ni = n > 1 ? n - 1 : 1;
+    k_compress<<<grid_for(ni, T, s->num_sms), T, 0, st>>>(ni, s->nodes, s->nodeh);
     RGX_CUDA(s, cudaGetLastError());
     return RGX_OK;
 }

@@ -33,6 +33,7 @@
 // local-frame moments A0, V = sum w y, P = sum w y y^T that are added atomically
 // per Gaussian.  k_grad_finalize chains them to mu, s, q, sigma~ once per Gaussian.
 #include <stdio.h>
+#include <cuda_fp16.h>
 #include "common.cuh"
 
 #define FULLMASK 0xffffffffu
@@ -41,6 +42,7 @@
 #define WARPS (RGX_BLOCK / 32)
 #define STK 256                                     // per-warp traversal stack
 #define CANDS 128                                   // pending leaf candidates (< 32 left + 64 new)
+#define CUT 32                                      // child records of a tile's BVH cut
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -48,6 +50,7 @@ struct MarchParams {
     const float4* __restrict__ sph;
     const int32_t* __restrict__ perm;
     const float4* __restrict__ nodes;
+    const uint4* __restrict__ nodeh;
     const float* __restrict__ root;
     const rgx_camera* __restrict__ cams;
     int64_t n;
@@ -93,10 +96,12 @@ struct WS {
     uint32_t* cand; // [CANDS] leaf candidates awaiting the sphere test
     uint32_t* surv; // [CANDS] sphere survivors awaiting the exact chord
     float* Y;       // [16] SH basis of the current ray direction
+    uint4* cut;     // [CUT] the tile's BVH cut: compressed child records (box, ref)
+    int* ncut;      // [1]   its size
 };
 
 __host__ __device__ inline size_t warp_bytes(int cap, bool bwd) {
-    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + 2 * CANDS * 4 + 16 * 4;
+    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + 2 * CANDS * 4 + CUT * 16 + 16 * 4 + 16;
     if (bwd) b += (size_t)cap * (16 + 8) + 32 * 16;
     return (b + 15) & ~(size_t)15;
 }
@@ -106,6 +111,7 @@ __device__ inline WS carve(char* base, int cap, bool bwd) {
     char* p = base;
     w.q = (float4*)p; p += (size_t)cap * 16;
     w.c = (float4*)p; p += (size_t)cap * 16;
+    w.cut = (uint4*)p; p += CUT * 16;
     if (bwd) { w.acc = (float4*)p; p += (size_t)cap * 16; w.bg = (float4*)p; p += 32 * 16; }
     else { w.acc = nullptr; w.bg = nullptr; }
     w.tio = (float2*)p; p += (size_t)cap * 8;
@@ -116,7 +122,8 @@ __device__ inline WS carve(char* base, int cap, bool bwd) {
     w.stk = (uint32_t*)p; p += (size_t)STK * 4;
     w.cand = (uint32_t*)p; p += CANDS * 4;
     w.surv = (uint32_t*)p; p += CANDS * 4;
-    w.Y = (float*)p;
+    w.Y = (float*)p; p += 16 * 4;
+    w.ncut = (int*)p;
     return w;
 }
 
@@ -131,6 +138,15 @@ __device__ __forceinline__ bool box_overlap(float4 lo, float4 hi, const Ray& r, 
     float t1 = fminf(fminf((fx - r.ox) * r.ix, (fy - r.oy) * r.iy), fminf((fz - r.oz) * r.iz, tb));
     tentry = t0;
     return t0 <= t1;
+}
+
+// One child of a compressed node: its box (halves -> floats) and its ref.
+__device__ __forceinline__ void child_of(uint4 v, float4& lo, float4& hi) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    const float2 c = __half22float2(*reinterpret_cast<const __half2*>(&v.z));
+    lo = make_float4(a.x, a.y, b.x, 0.0f);
+    hi = make_float4(b.y, c.x, c.y, 0.0f);
 }
 
 // Exact chord of the Q_eps ellipsoid of Gaussian p: q(t) = qmin + a (t - tc)^2.
@@ -235,9 +251,28 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
                          bool chunked, OnFull on_full, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    if (lane == 0) W.stk[0] = 0u;
+    int sp = 0, npend = 0, nsurv = 0, ncol = nL;  // entries [ncol, nL) still need their colour
+    // first step: the tile's cut (boxes in shared memory) instead of the root
+    const int ncut = *W.ncut;
+    for (int b0 = 0; b0 < ncut; b0 += 32) {
+        bool h = false;
+        uint32_t rf = 0;
+        if (b0 + lane < ncut) {
+            const uint4 v = W.cut[b0 + lane];
+            float4 lo, hi;
+            child_of(v, lo, hi);
+            float te;
+            h = box_overlap(lo, hi, r, ta, tb, te);
+            rf = v.w;
+        }
+        const bool pi = h && !(rf & LEAF_BIT), pl = h && (rf & LEAF_BIT);
+        const uint32_t bi = __ballot_sync(FULLMASK, pi), bl = __ballot_sync(FULLMASK, pl);
+        if (pi) W.stk[sp + __popc(bi & lt)] = rf;
+        if (pl) W.cand[npend + __popc(bl & lt)] = rf & ~LEAF_BIT;
+        sp += __popc(bi);
+        npend += __popc(bl);
+    }
     __syncwarp();
-    int sp = 1, npend = 0, nsurv = 0, ncol = nL;  // entries [ncol, nL) still need their colour
     while (sp > 0 || npend > 0 || nsurv > 0) {
         if (sp > 0) {
             // wide pops while the stack has room, then depth-first with a reserve
@@ -255,14 +290,15 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
             uint32_t rl = 0, rr = 0;
             if (lane < take) {
                 cnt.visits++;
-                const float4* nd = P.nodes + 4 * (size_t)ref;
-                const float4 a0 = __ldg(nd), a1 = __ldg(nd + 1), a2 = __ldg(nd + 2), a3 = __ldg(nd + 3);
-                const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
+                const uint4 vl = __ldg(P.nodeh + 2 * (size_t)ref), vr = __ldg(P.nodeh + 2 * (size_t)ref + 1);
+                float4 llo, lhi, rlo, rhi;
+                child_of(vl, llo, lhi);
+                child_of(vr, rlo, rhi);
                 float te;
-                hl_ = box_overlap(a0, a1, r, ta, tb, te);
-                hr_ = box_overlap(a2, a3, r, ta, tb, te);
-                rl = (first == split) ? (split | LEAF_BIT) : split;
-                rr = (split + 1 == last) ? ((split + 1) | LEAF_BIT) : (split + 1);
+                hl_ = box_overlap(llo, lhi, r, ta, tb, te);
+                hr_ = box_overlap(rlo, rhi, r, ta, tb, te);
+                rl = vl.w;
+                rr = vr.w;
             }
             const bool pl = hl_ && !(rl & LEAF_BIT), pr = hr_ && !(rr & LEAF_BIT);
             const bool ll = hl_ && (rl & LEAF_BIT), lr = hr_ && (rr & LEAF_BIT);
@@ -355,13 +391,45 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
 // ClosestHit(ta) = min over Gaussians whose chord has t_out > ta and t_in < tf of
 // max(t_in, ta); tf if there is none (Algorithm 1, Eq. 4).  Cooperative
 // traversal pruned by the warp's best value, near children on top of the stack.
+// Called with tf replaced by a smaller limit it returns the same minimum if one
+// lies below the limit, else the limit itself.
 __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, float ta, float tf, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    if (lane == 0) { cnt.chq++; W.stk[0] = 0u; W.stkt[0] = -INFINITY; }
-    __syncwarp();
-    int sp = 1;
+    if (lane == 0) cnt.chq++;
+    int sp = 0;
     float best = tf;
+    // first step: the tile's cut (boxes in shared memory) instead of the root
+    const int ncut = *W.ncut;
+    for (int b0 = 0; b0 < ncut; b0 += 32) {
+        bool h = false;
+        uint32_t rf = 0;
+        float te = INFINITY, cand = INFINITY;
+        if (b0 + lane < ncut) {
+            const uint4 v = W.cut[b0 + lane];
+            float4 lo, hi;
+            child_of(v, lo, hi);
+            h = box_overlap(lo, hi, r, ta, tf, te);
+            rf = v.w;
+            if (h && (rf & LEAF_BIT)) {
+                const uint32_t leaf = rf & ~LEAF_BIT;
+                const int64_t p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
+                const Chord c = chord_of(P.geom, p, r);
+                if (c.ok && c.tout > ta && c.tin < tf) cand = fmaxf(c.tin, ta);
+            }
+        }
+        best = fminf(best, warp_min(cand));
+        if (best <= ta) return ta;
+        const bool pi = h && !(rf & LEAF_BIT) && te < best;
+        const uint32_t bi = __ballot_sync(FULLMASK, pi);
+        if (pi) {
+            const int o = sp + __popc(bi & lt);
+            W.stk[o] = rf;
+            W.stkt[o] = te;
+        }
+        sp += __popc(bi);
+    }
+    __syncwarp();
     while (sp > 0) {
         const int take = STK - sp >= 2 ? min(min(sp, 32), max((STK - 100 - sp) / 2, 1)) : 0;
         if (take <= 0) {
@@ -380,13 +448,14 @@ __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, floa
         float tl = INFINITY, tr = INFINITY;
         if (active) {
             cnt.visits++;
-            const float4* nd = P.nodes + 4 * (size_t)ref;
-            const float4 a0 = __ldg(nd), a1 = __ldg(nd + 1), a2 = __ldg(nd + 2), a3 = __ldg(nd + 3);
-            const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
-            hl_ = box_overlap(a0, a1, r, ta, best, tl);
-            hr_ = box_overlap(a2, a3, r, ta, best, tr);
-            rl = (first == split) ? (split | LEAF_BIT) : split;
-            rr = (split + 1 == last) ? ((split + 1) | LEAF_BIT) : (split + 1);
+            const uint4 vl = __ldg(P.nodeh + 2 * (size_t)ref), vr = __ldg(P.nodeh + 2 * (size_t)ref + 1);
+            float4 llo, lhi, rlo, rhi;
+            child_of(vl, llo, lhi);
+            child_of(vr, rlo, rhi);
+            hl_ = box_overlap(llo, lhi, r, ta, best, tl);
+            hr_ = box_overlap(rlo, rhi, r, ta, best, tr);
+            rl = vl.w;
+            rr = vr.w;
 #pragma unroll
             for (int side = 0; side < 2; side++) {
                 const bool h = side ? hr_ : hl_;
@@ -428,7 +497,28 @@ __device__ __forceinline__ void eval_entries(const WS& W, bool idx, int m, float
     const int lane = threadIdx.x & 31;
     const int k = lane % NS, grp = lane / NS;
     const float half = __fmul_rn(0.5f, dtk);
-    for (int h = grp; h < m; h += G) {
+    const float base = __fadd_rn(tS, half);  // t of sample 0
+    // four hits per iteration, all shared-memory loads issued before the math
+    int h = grp;
+    for (; h + 3 * G < m; h += 4 * G) {
+        uint32_t e[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) e[i] = idx ? W.seg[h + i * G] : (uint32_t)(h + i * G);
+        float4 q4[4], c4[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) { q4[i] = W.q[e[i]]; c4[i] = W.c[e[i]]; }
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const float u = __fmaf_rn((float)k, dtk, __fadd_rn(__fsub_rn(tS, q4[i].x), half));
+            const float q = __fmaf_rn(__fmul_rn(q4[i].y, u), u, q4[i].z);
+            const float g = q <= q4[i].w ? exp2f(__fmaf_rn(q, NEG_HALF_LOG2E, c4[i].x)) : 0.0f;
+            sig = __fadd_rn(sig, g);
+            S0 = __fmaf_rn(g, c4[i].y, S0);
+            S1 = __fmaf_rn(g, c4[i].z, S1);
+            S2 = __fmaf_rn(g, c4[i].w, S2);
+        }
+    }
+    for (; h < m; h += G) {
         const uint32_t e = idx ? W.seg[h] : (uint32_t)h;
         const float4 q4 = W.q[e];
         const float u = __fmaf_rn((float)k, dtk, __fadd_rn(__fsub_rn(tS, q4.x), half));
@@ -442,6 +532,7 @@ __device__ __forceinline__ void eval_entries(const WS& W, bool idx, int m, float
             S2 = __fmaf_rn(g, c4.w, S2);
         }
     }
+    (void)base;
 }
 
 // Adjoint, hit-parallel: per entry, accumulate over the segment's samples
@@ -524,38 +615,28 @@ __device__ void flush_entries(const MarchParams& P, const WS& W, const Ray& r, i
 }
 
 // ------------------------------------------------------------------ one ray, one warp
-template <int NS, bool BWD>
-__device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const rgx_camera& C, int px, int py,
-                          Counters& cnt, float4& o_rgba, float4& o_state, int& o_nrec) {
-    const int lane = threadIdx.x & 31;
-    const int k = lane % NS;
-    const int cap = P.hit_cap;
-    // ---- ray (pinhole, OpenCV convention); every lane holds the same values
+// Ray through the centre of pixel (px, py) (pinhole, OpenCV convention); every
+// lane holds the same values.
+__device__ __forceinline__ Ray make_ray(const rgx_camera& C, int px, int py) {
     Ray r;
-    {
-        const float ux = ((float)px + 0.5f - C.cx) / C.fx;
-        const float vy = ((float)py + 0.5f - C.cy) / C.fy;
-        float dx = C.c2w[0] * ux + C.c2w[1] * vy + C.c2w[2];
-        float dy = C.c2w[4] * ux + C.c2w[5] * vy + C.c2w[6];
-        float dz = C.c2w[8] * ux + C.c2w[9] * vy + C.c2w[10];
-        const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-        r.dx = dx * inv; r.dy = dy * inv; r.dz = dz * inv;
-        r.ox = C.c2w[3]; r.oy = C.c2w[7]; r.oz = C.c2w[11];
-        const float tiny = 1e-20f;
-        r.ix = 1.0f / (fabsf(r.dx) > tiny ? r.dx : copysignf(tiny, r.dx));
-        r.iy = 1.0f / (fabsf(r.dy) > tiny ? r.dy : copysignf(tiny, r.dy));
-        r.iz = 1.0f / (fabsf(r.dz) > tiny ? r.dz : copysignf(tiny, r.dz));
-    }
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Tf = 1.f, dTcoef = 0.f;
-    if (BWD) {
-        const float4 up = P.d_rgba[ray];
-        if (up.x == 0.0f && up.y == 0.0f && up.z == 0.0f && up.w == 0.0f) return;
-        a0 = up.x; a1 = up.y; a2 = up.z;
-        const float4 st = P.state[ray];
-        Cf0 = st.x; Cf1 = st.y; Cf2 = st.z; Tf = st.w;
-        dTcoef = (a0 * P.bg0 + a1 * P.bg1 + a2 * P.bg2 - up.w) * Tf;
-    }
-    // ---- bounds: t_n, and t_f = camera t_far or the exit of the scene box
+    const float ux = ((float)px + 0.5f - C.cx) / C.fx;
+    const float vy = ((float)py + 0.5f - C.cy) / C.fy;
+    float dx = C.c2w[0] * ux + C.c2w[1] * vy + C.c2w[2];
+    float dy = C.c2w[4] * ux + C.c2w[5] * vy + C.c2w[6];
+    float dz = C.c2w[8] * ux + C.c2w[9] * vy + C.c2w[10];
+    const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
+    r.dx = dx * inv; r.dy = dy * inv; r.dz = dz * inv;
+    r.ox = C.c2w[3]; r.oy = C.c2w[7]; r.oz = C.c2w[11];
+    const float tiny = 1e-20f;
+    r.ix = 1.0f / (fabsf(r.dx) > tiny ? r.dx : copysignf(tiny, r.dx));
+    r.iy = 1.0f / (fabsf(r.dy) > tiny ? r.dy : copysignf(tiny, r.dy));
+    r.iz = 1.0f / (fabsf(r.dz) > tiny ? r.dz : copysignf(tiny, r.dz));
+    return r;
+}
+
+// t_f: the camera's t_far, or (t_far <= 0) the exit of the scene box (t_n when
+// the ray misses the box).
+__device__ __forceinline__ float far_bound(const MarchParams& P, const rgx_camera& C, const Ray& r) {
     const float tn = C.t_near;
     float tf = C.t_far;
     if (!(tf > 0.0f)) {
@@ -567,6 +648,28 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         const float texit = fminf(fminf((fx - r.ox) * r.ix, (fy - r.oy) * r.iy), (fz - r.oz) * r.iz);
         tf = (in && texit > tn) ? texit : tn;
     }
+    return tf;
+}
+
+template <int NS, bool BWD>
+__device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const rgx_camera& C, int px, int py,
+                          Counters& cnt, float4& o_rgba, float4& o_state, int& o_nrec) {
+    const int lane = threadIdx.x & 31;
+    const int k = lane % NS;
+    const int cap = P.hit_cap;
+    const Ray r = make_ray(C, px, py);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Tf = 1.f, dTcoef = 0.f;
+    if (BWD) {
+        const float4 up = P.d_rgba[ray];
+        if (up.x == 0.0f && up.y == 0.0f && up.z == 0.0f && up.w == 0.0f) return;
+        a0 = up.x; a1 = up.y; a2 = up.z;
+        const float4 st = P.state[ray];
+        Cf0 = st.x; Cf1 = st.y; Cf2 = st.z; Tf = st.w;
+        dTcoef = (a0 * P.bg0 + a1 * P.bg1 + a2 * P.bg2 - up.w) * Tf;
+    }
+    // ---- bounds: t_n, and t_f = camera t_far or the exit of the scene box
+    const float tn = C.t_near;
+    const float tf = far_bound(P, C, r);
     {
         float Y[16];
         sh_basis16(r.dx, r.dy, r.dz, Y);
@@ -812,6 +915,151 @@ __device__ __forceinline__ bool tile_pixel(const rgx_camera& cam, uint32_t lt, i
     return px < cam.width && py < cam.height;
 }
 
+// ------------------------------------------------------------------ tile cut
+// Conservative view cone of the pixel rectangle [pxa, pxb] x [pya, pyb]: four
+// planes through the camera centre, each spanned by two corner rays of the
+// rectangle's outer pixel boundaries (half a pixel beyond the outermost ray),
+// oriented so that the centre ray is inside.  Any invertible c2w rotation part.
+struct Frustum {
+    float4 pl[4];  // (n, -n.o): a point x is inside a plane when n.x - n.o >= 0
+};
+
+__device__ __forceinline__ float3 cam_dir(const rgx_camera& C, float u, float v) {
+    return make_float3(C.c2w[0] * u + C.c2w[1] * v + C.c2w[2], C.c2w[4] * u + C.c2w[5] * v + C.c2w[6],
+                       C.c2w[8] * u + C.c2w[9] * v + C.c2w[10]);
+}
+
+__device__ Frustum tile_frustum(const rgx_camera& C, int pxa, int pya, int pxb, int pyb) {
+    const float u0 = ((float)pxa - C.cx) / C.fx, u1 = ((float)pxb + 1.0f - C.cx) / C.fx;
+    const float v0 = ((float)pya - C.cy) / C.fy, v1 = ((float)pyb + 1.0f - C.cy) / C.fy;
+    const float3 d00 = cam_dir(C, u0, v0), d10 = cam_dir(C, u1, v0), d01 = cam_dir(C, u0, v1),
+                 d11 = cam_dir(C, u1, v1);
+    const float3 dc = cam_dir(C, 0.5f * (u0 + u1), 0.5f * (v0 + v1));
+    const float ox = C.c2w[3], oy = C.c2w[7], oz = C.c2w[11];
+    const float3 ea[4] = {d00, d10, d00, d01}, eb[4] = {d01, d11, d10, d11};
+    Frustum F;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float nx = ea[i].y * eb[i].z - ea[i].z * eb[i].y;
+        float ny = ea[i].z * eb[i].x - ea[i].x * eb[i].z;
+        float nz = ea[i].x * eb[i].y - ea[i].y * eb[i].x;
+        if (nx * dc.x + ny * dc.y + nz * dc.z < 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
+        F.pl[i] = make_float4(nx, ny, nz, -(nx * ox + ny * oy + nz * oz));
+    }
+    return F;
+}
+
+// Box entirely on the outer side of one plane (beyond a rounding allowance).
+// Empty (inverted) boxes give inf / NaN sums and are kept; the ray test drops them.
+__device__ __forceinline__ bool box_outside(const Frustum& F, float4 lo, float4 hi) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const float4 p = F.pl[i];
+        const float x = p.x > 0.0f ? hi.x : lo.x, y = p.y > 0.0f ? hi.y : lo.y, z = p.z > 0.0f ? hi.z : lo.z;
+        const float v = p.x * x + p.y * y + p.z * z + p.w;
+        const float mag = fabsf(p.x * x) + fabsf(p.y * y) + fabsf(p.z * z) + fabsf(p.w);
+        if (v < -1e-5f * mag) return true;
+    }
+    return false;
+}
+
+// The tile's BVH cut: a set of at most CUT child records (compressed box + ref)
+// whose subtrees hold every leaf whose box meets the view cone.  Starts from the
+// root's two children and replaces internal records by their children inside
+// the cone, level by level, while the set stays within CUT; records outside the
+// cone are dropped.  Every traversal of the tile's rays starts from it.
+#define CUT_LEVELS 48
+#define CUT_R (CUT / 32)
+__device__ void build_cut(const MarchParams& P, const WS& W, const Frustum& F, Counters& cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    bool keep = false;
+    if (lane < 2) {
+        v = __ldg(P.nodeh + lane);
+        float4 lo, hi;
+        child_of(v, lo, hi);
+        keep = !box_outside(F, lo, hi);
+    }
+    const uint32_t b = __ballot_sync(FULLMASK, keep);
+    if (keep) W.cut[__popc(b & lt)] = v;
+    int nc = __popc(b);
+    __syncwarp();
+    for (int it = 0; it < CUT_LEVELS; it++) {
+        // record i = 32 j + lane
+        uint4 mine[CUT_R], c0[CUT_R], c1[CUT_R];
+        bool internal[CUT_R], k0[CUT_R], k1[CUT_R];
+#pragma unroll
+        for (int j = 0; j < CUT_R; j++) {
+            const int i = 32 * j + lane;
+            mine[j] = i < nc ? W.cut[i] : make_uint4(0u, 0u, 0u, LEAF_BIT);
+            internal[j] = i < nc && !(mine[j].w & LEAF_BIT);
+            c0[j] = make_uint4(0u, 0u, 0u, 0u);
+            c1[j] = c0[j];
+            k0[j] = k1[j] = false;
+            if (internal[j]) {
+                cnt.visits++;
+                c0[j] = __ldg(P.nodeh + 2 * (size_t)mine[j].w);
+                c1[j] = __ldg(P.nodeh + 2 * (size_t)mine[j].w + 1);
+            }
+        }
+        // a record grows the set by add = (children kept) - 1; shrinking ones always
+        // expand, growing ones while the running total of growth (in record order) fits
+        bool expand[CUT_R];
+        bool anyx = false;
+        int run = 0;
+#pragma unroll
+        for (int j = 0; j < CUT_R; j++) {
+            if (internal[j]) {
+                float4 lo, hi;
+                child_of(c0[j], lo, hi);
+                k0[j] = !box_outside(F, lo, hi);
+                child_of(c1[j], lo, hi);
+                k1[j] = !box_outside(F, lo, hi);
+            }
+            const int add = internal[j] ? (int)k0[j] + (int)k1[j] - 1 : 0;
+            int pre = add > 0 ? add : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(FULLMASK, pre, d);
+                if (lane >= d) pre += t;
+            }
+            expand[j] = internal[j] && (add <= 0 || nc + run + pre <= CUT);
+            run += __shfl_sync(FULLMASK, pre, 31);
+            anyx |= expand[j];
+        }
+        if (!__any_sync(FULLMASK, anyx)) break;
+        int off[CUT_R], mcount[CUT_R];
+        int total = 0;
+#pragma unroll
+        for (int j = 0; j < CUT_R; j++) {
+            mcount[j] = expand[j] ? (int)k0[j] + (int)k1[j] : (32 * j + lane < nc ? 1 : 0);
+            int o = mcount[j];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int t = __shfl_up_sync(FULLMASK, o, d);
+                if (lane >= d) o += t;
+            }
+            off[j] = total + o - mcount[j];
+            total += __shfl_sync(FULLMASK, o, 31);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < CUT_R; j++) {
+            if (expand[j]) {
+                if (k0[j]) W.cut[off[j]] = c0[j];
+                if (k1[j]) W.cut[off[j] + (k0[j] ? 1 : 0)] = c1[j];
+            } else if (32 * j + lane < nc) {
+                W.cut[off[j]] = mine[j];
+            }
+        }
+        nc = total;
+        __syncwarp();
+    }
+    if (lane == 0) *W.ncut = nc;
+    __syncwarp();
+}
+
 template <int NS, bool BWD>
 __global__ void __launch_bounds__(RGX_BLOCK) k_march(MarchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -845,6 +1093,32 @@ __global__ void __launch_bounds__(RGX_BLOCK) k_march(MarchParams P) {
         Counters cnt = {0, 0, 0, 0, 0, 0, 0};
         float4 my_rgba = make_float4(0.f, 0.f, 0.f, 0.f), my_state = my_rgba;
         int my_nrec = 0;
+        bool work = P.n > 0;
+        if (BWD && work) {
+            // the adjoint skips tiles whose rays all have a zero upstream gradient
+            int px, py;
+            bool nz = false;
+            if (tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
+                const float4 up = P.d_rgba[(int64_t)s_pix[c] + (int64_t)py * cam.width + px];
+                nz = up.x != 0.0f || up.y != 0.0f || up.z != 0.0f || up.w != 0.0f;
+            }
+            work = __any_sync(FULLMASK, nz);
+        }
+        if (work) {
+            int pxa, pya, pxb, pyb;
+            if (zt) {
+                tile_pixel(cam, lt, 0, zt, P.tile_w, P.tile_h, pxa, pya);
+                pxb = pxa + P.tile_w - 1;
+                pyb = pya + P.tile_h - 1;
+            } else {
+                const int64_t p0 = (int64_t)lt * 32, p1 = p0 + 31;
+                pya = (int)(p0 / cam.width);
+                pyb = (int)(p1 / cam.width);
+                if (pya == pyb) { pxa = (int)(p0 % cam.width); pxb = (int)(p1 % cam.width); }
+                else { pxa = 0; pxb = cam.width - 1; }
+            }
+            build_cut(P, W, tile_frustum(cam, pxa, pya, pxb, pyb), cnt);
+        }
         for (int l = 0; l < 32; l++) {
             int px, py;
             if (!tile_pixel(cam, lt, l, zt, P.tile_w, P.tile_h, px, py)) continue;
@@ -985,7 +1259,7 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
                                int32_t* sched_n, cudaStream_t st) {
     MarchParams P;
     memset(&P, 0, sizeof P);
-    P.geom = s->geom; P.shc = s->shc; P.sph = s->sph; P.perm = s->perm; P.nodes = s->nodes; P.root = s->root;
+    P.geom = s->geom; P.shc = s->shc; P.sph = s->sph; P.perm = s->perm; P.nodes = s->nodes; P.nodeh = s->nodeh; P.root = s->root;
     P.n = s->n; P.morton = s->morton;
     P.cams = s->cams; P.ncam = ncam;
     P.flags = o->flags;
