@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-tune", action="store_true",
                    help="skip rgx_autotune (tile shape and hit_cap; N_S fixed) before the timed steps")
+    p.add_argument("--tile", default=None, help="fixed ray-tile shape WxH (skips rgx_autotune)")
+    p.add_argument("--hit-cap", type=int, default=None, help="fixed hit-list capacity (skips rgx_autotune)")
     p.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_1m", "sweep_6m"],
                    help="extra measurements: batch_1m = 8 uneven views, autotuned, CUDA-graph captured "
                         "fwd+bwd; sweep_6m = 64 views forward, one persistent launch vs one launch per view")
@@ -188,7 +190,13 @@ def run_rgx(args, rank, world, local):
     grads = [torch.zeros_like(x) for x in t]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     tuned = None
-    if not args.no_tune:
+    if args.tile or args.hit_cap:
+        if args.tile:
+            opts.tile_w, opts.tile_h = (int(x) for x in args.tile.lower().split("x"))
+        if args.hit_cap:
+            opts.hit_cap = args.hit_cap
+        tuned = {"tile": [opts.tile_w, opts.tile_h], "hit_cap": opts.hit_cap, "fixed": True}
+    elif not args.no_tune:
         # implementation knobs only (tile shape, hit-list capacity); N_S stays the workload's
         sc.build(*t, opts)
         best, tune_ms = sc.autotune(cams, opts, tune_ns=False, with_backward=True)
