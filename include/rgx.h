@@ -123,7 +123,9 @@ rgx_status rgx_build_bvh(rgx_scene* scene, int64_t n, int32_t sh_degree,
  *   rgba       [R,4]        output, R = sum_c width_c*height_c, camera-major,
  *                           row-major pixels: (C + T bg, 1 - T)
  *   fwd_state  [R] x rgx_fwd_state_bytes()  per-ray (C, T) kept for the adjoint
- *                           (may be NULL for inference)
+ *                           (may be NULL for inference); opaque: the sign bit of
+ *                           T records which collection path the ray took, so that
+ *                           the adjoint replays it
  */
 rgx_status rgx_render_forward(rgx_scene* scene, const rgx_camera* cams, int32_t ncam,
                               const rgx_opts* opts, float* rgba, void* fwd_state, void* stream);

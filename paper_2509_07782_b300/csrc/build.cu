@@ -325,23 +325,61 @@ __global__ void k_single(const float4* __restrict__ leafbox, float4* nodes, floa
     root[0] = lo.x; root[1] = lo.y; root[2] = lo.z; root[3] = hi.x; root[4] = hi.y; root[5] = hi.z;
 }
 
-// Half-precision copy of the refitted nodes for the traversals (outward rounding).
+// 4-wide traversal nodes.  Every internal node i of the binary radix tree gets a
+// record of (up to) four children: its grandchildren, or a child itself where that
+// child is a leaf.  A traversal that pushes the internal ids found in a record and
+// later reads their records visits the binary tree two levels per fetch.  Each
+// child is 16 B: its box (the refitted box, or a leaf's minimal AABB) as 6 halves
+// rounded outward (lo down, hi up) and a ref = binary node id for an internal
+// child, packed index | 0x80000000 for a leaf.  Unused slots, and empty Gaussians,
+// hold an inverted box (lo = +inf, hi = -inf) that every ray misses.
 __device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
     return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
 }
 
-__global__ void k_compress(int64_t n_internal, const float4* __restrict__ nodes, uint4* __restrict__ nodeh) {
+__device__ __forceinline__ uint4 box_record(float4 lo, float4 hi, uint32_t ref) {
+    return make_uint4(pack_h2(__float2half_rd(lo.x), __float2half_rd(lo.y)),
+                      pack_h2(__float2half_rd(lo.z), __float2half_ru(hi.x)),
+                      pack_h2(__float2half_ru(hi.y), __float2half_ru(hi.z)), ref);
+}
+
+__device__ __forceinline__ uint4 child_record(int64_t n, int morton, const int32_t* __restrict__ perm, float4 lo,
+                                              float4 hi, bool leaf, int64_t c) {
+    if (!leaf) return box_record(lo, hi, (uint32_t)c);
+    if (c >= n)  // the missing second leaf of a 1-Gaussian tree
+        return box_record(make_float4(INFINITY, INFINITY, INFINITY, 0.f), make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f),
+                          0xffffffffu);
+    const uint32_t p = morton ? (uint32_t)c : (uint32_t)perm[c];
+    return box_record(lo, hi, p | 0x80000000u);
+}
+
+__global__ void k_widen(int64_t n_internal, int64_t n, int morton, const float4* __restrict__ nodes,
+                        const int32_t* __restrict__ perm, uint4* __restrict__ nodew) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_internal; i += (int64_t)gridDim.x * blockDim.x) {
         const float4 a0 = nodes[4 * i], a1 = nodes[4 * i + 1], a2 = nodes[4 * i + 2], a3 = nodes[4 * i + 3];
-        const uint32_t first = __float_as_uint(a0.w), split = __float_as_uint(a1.w), last = __float_as_uint(a2.w);
-        const uint32_t rl = (first == split) ? (split | 0x80000000u) : split;
-        const uint32_t rr = (split + 1 == last) ? ((split + 1) | 0x80000000u) : (split + 1);
-        nodeh[2 * i] = make_uint4(pack_h2(__float2half_rd(a0.x), __float2half_rd(a0.y)),
-                                  pack_h2(__float2half_rd(a0.z), __float2half_ru(a1.x)),
-                                  pack_h2(__float2half_ru(a1.y), __float2half_ru(a1.z)), rl);
-        nodeh[2 * i + 1] = make_uint4(pack_h2(__float2half_rd(a2.x), __float2half_rd(a2.y)),
-                                      pack_h2(__float2half_rd(a2.z), __float2half_ru(a3.x)),
-                                      pack_h2(__float2half_ru(a3.y), __float2half_ru(a3.z)), rr);
+        const int first = __float_as_int(a0.w), split = __float_as_int(a1.w), last = __float_as_int(a2.w);
+        uint4 rec[4];
+        int k = 0;
+#pragma unroll
+        for (int side = 0; side < 2; side++) {
+            const int c = split + side;
+            const bool leaf = side ? (c == last) : (first == c);
+            if (leaf) {
+                rec[k++] = side ? child_record(n, morton, perm, a2, a3, true, c)
+                                : child_record(n, morton, perm, a0, a1, true, c);
+            } else {
+                const float4 c0 = nodes[4 * (int64_t)c], c1 = nodes[4 * (int64_t)c + 1];
+                const float4 c2 = nodes[4 * (int64_t)c + 2], c3 = nodes[4 * (int64_t)c + 3];
+                const int cf = __float_as_int(c0.w), cs = __float_as_int(c1.w), cl = __float_as_int(c2.w);
+                rec[k++] = child_record(n, morton, perm, c0, c1, cf == cs, cs);
+                rec[k++] = child_record(n, morton, perm, c2, c3, cs + 1 == cl, cs + 1);
+            }
+        }
+        for (int j = k; j < 4; j++)
+            rec[j] = box_record(make_float4(INFINITY, INFINITY, INFINITY, 0.f),
+                                make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f), 0xffffffffu);
+#pragma unroll
+        for (int j = 0; j < 4; j++) nodew[4 * i + j] = rec[j];
     }
 }
 
@@ -372,7 +410,7 @@ rgx_status rgx_internal_reserve(rgx_scene* s, int64_t n) {
     e = e ? e : grow(&s->keys[0], c); e = e ? e : grow(&s->keys[1], c);
     e = e ? e : grow(&s->vals[0], c); e = e ? e : grow(&s->vals[1], c);
     e = e ? e : grow(&s->nodes, 4 * (size_t)c);
-    e = e ? e : grow(&s->nodeh, 2 * (size_t)c);
+    e = e ? e : grow(&s->nodew, 4 * (size_t)c);
     e = e ? e : grow(&s->parent, 2 * (size_t)c);
     e = e ? e : grow(&s->visit, (size_t)c);
     e = e ? e : grow(&s->geom, 4 * (size_t)c);
@@ -444,7 +482,7 @@ extern "C" rgx_status rgx_build_bvh(rgx_scene* s, int64_t n, int32_t sh_degree, 
         k_refit<<<g, T, 0, st>>>(n, s->leafbox, s->nodes, s->parent, s->visit, s->root);
     }
     const int64_t ni = n > 1 ? n - 1 : 1;
-    k_compress<<<grid_for(ni, T, s->num_sms), T, 0, st>>>(ni, s->nodes, s->nodeh);
+    k_widen<<<grid_for(ni, T, s->num_sms), T, 0, st>>>(ni, n, s->morton, s->nodes, s->perm, s->nodew);
     RGX_CUDA(s, cudaGetLastError());
     return RGX_OK;
 }

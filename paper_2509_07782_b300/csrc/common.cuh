@@ -18,10 +18,11 @@
 //   node[4i+2] = (right.lo xyz, last)    right child = split+1 (leaf iff split+1 == last)
 //   node[4i+3] = (right.hi xyz, 0)
 //
-// Compressed copy read by the traversals: nodeh[2i] = (left box as 6 halves,
-// left ref), nodeh[2i+1] = (right box as 6 halves, right ref), 32 B per node.
-// Halves are rounded outward (lo down, hi up), so the boxes stay conservative;
-// ref = leaf index | 0x80000000 for a leaf, else the internal node id.
+// 4-wide copy read by the traversals: nodew[4i .. 4i+3] = the (up to) four
+// grandchildren of internal node i (a child itself where it is a leaf), 16 B each:
+// the child's box as 6 halves rounded outward (so it stays conservative) and a ref
+// = internal node id, or packed index | 0x80000000 for a leaf.  Unused slots hold
+// an inverted (empty) box.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -48,7 +49,7 @@ struct rgx_scene {
     int sorted_buf = 0;       // which of keys/vals holds the sorted result
     uint32_t* hist = nullptr; size_t hist_cap = 0;
     float4* nodes = nullptr;
-    uint4* nodeh = nullptr;        // [2 (n-1)] compressed nodes for traversal
+    uint4* nodew = nullptr;        // [4 (n-1)] 4-wide traversal records
     int32_t* parent = nullptr;     // [2n]: parent of leaf i at [i], of internal j at [n+j]
     int32_t* visit = nullptr;      // [n] refit arrival counters
     float4* geom = nullptr;

@@ -40,8 +40,9 @@
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
 #define WARPS (RGX_BLOCK / 32)
-#define STK 256                                     // per-warp traversal stack
-#define CANDS 128                                   // pending leaf candidates (< 32 left + 64 new)
+#define STK 320                                     // per-warp traversal stack
+#define STK_RES 152                                 // depth-first reserve: 3 x (4-wide depth bound 48) + 4
+#define SURV 160                                    // leaves awaiting their exact chord (< 32 left + 128 new)
 #define CUT 32                                      // child records of a tile's BVH cut
 
 struct MarchParams {
@@ -50,7 +51,7 @@ struct MarchParams {
     const float4* __restrict__ sph;
     const int32_t* __restrict__ perm;
     const float4* __restrict__ nodes;
-    const uint4* __restrict__ nodeh;
+    const uint4* __restrict__ nodew;
     const float* __restrict__ root;
     const rgx_camera* __restrict__ cams;
     int64_t n;
@@ -93,15 +94,14 @@ struct WS {
     uint32_t* seg;  // [cap] entries of the current segment
     uint32_t* stk;  // [STK] node refs
     float* stkt;    // [STK] entry distance (nearest-hit traversal)
-    uint32_t* cand; // [CANDS] leaf candidates awaiting the sphere test
-    uint32_t* surv; // [CANDS] sphere survivors awaiting the exact chord
+    uint32_t* surv; // [SURV] leaves whose box meets the ray, awaiting the exact chord
     float* Y;       // [16] SH basis of the current ray direction
     uint4* cut;     // [CUT] the tile's BVH cut: compressed child records (box, ref)
     int* ncut;      // [1]   its size
 };
 
 __host__ __device__ inline size_t warp_bytes(int cap, bool bwd) {
-    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + 2 * CANDS * 4 + CUT * 16 + 16 * 4 + 16;
+    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + SURV * 4 + CUT * 16 + 16 * 4 + 16;
     if (bwd) b += (size_t)cap * (16 + 8) + 32 * 16;
     return (b + 15) & ~(size_t)15;
 }
@@ -120,8 +120,7 @@ __device__ inline WS carve(char* base, int cap, bool bwd) {
     w.pid = (uint32_t*)p; p += (size_t)cap * 4;
     w.seg = (uint32_t*)p; p += (size_t)cap * 4;
     w.stk = (uint32_t*)p; p += (size_t)STK * 4;
-    w.cand = (uint32_t*)p; p += CANDS * 4;
-    w.surv = (uint32_t*)p; p += CANDS * 4;
+    w.surv = (uint32_t*)p; p += SURV * 4;
     w.Y = (float*)p; p += 16 * 4;
     w.ncut = (int*)p;
     return w;
@@ -229,13 +228,43 @@ struct NoChunk {
     __device__ void operator()(int) const {}
 };
 
+// Test of one 4-wide child record (a box for internal and leaf children alike)
+// against the ray over [ta, tb); te = entry distance.
+__device__ __forceinline__ bool record_hit(uint4 v, const Ray& r, float ta, float tb, float& te) {
+    float4 lo, hi;
+    child_of(v, lo, hi);
+    return box_overlap(lo, hi, r, ta, tb, te);
+}
+
+// Exclusive prefix sum over the warp; `total` receives the sum over all lanes.
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t& total) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULLMASK, x, d);
+        if (lane >= d) x += t;
+    }
+    total = __shfl_sync(FULLMASK, x, 31);
+    return x - v;
+}
+
+// Nodes to pop in one traversal step: up to 32 while the stack keeps room for
+// their (up to 4) children each above the depth-first reserve, then one at a
+// time; 0 when even that no longer fits (stack overflow).
+__device__ __forceinline__ int pop_count(int sp) {
+    if (STK - sp < 4) return 0;
+    return min(min(sp, 32), max((STK - STK_RES - sp) / 4, 1));
+}
+
 // Collect into the list every Gaussian whose exact chord overlaps [ta, tb).
-// Traversal steps pop up to 32 nodes; leaf candidates are queued and their
-// chords solved in full 32-lane rounds; SH colours are computed afterwards for
-// the kept (compacted) entries only.  Returns 0 when complete, 1 when the list
-// would overflow (window mode: the caller shrinks the window), 2 on a
-// traversal-stack overflow.  In chunked mode a full list is handed to
-// `on_full(m)` and reset instead.
+// Each traversal step pops up to 32 4-wide nodes (one per lane; a lane tests
+// the node's four child boxes).  Leaves whose box meets the ray are queued and
+// their exact chords solved in full 32-lane rounds; SH colours are computed
+// afterwards for the kept (compacted) entries only.  Returns 0
+// when complete, 1 when the list would overflow (window mode: the caller
+// shrinks the window), 2 on a traversal-stack overflow.  In chunked mode a full
+// list is handed to `on_full(m)` and reset instead.
 __device__ __forceinline__ void colour_entries(const MarchParams& P, const WS& W, int from, int to) {
     const int lane = threadIdx.x & 31;
     for (int e = from + lane; e < to; e += 32) {
@@ -251,33 +280,30 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
                          bool chunked, OnFull on_full, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    int sp = 0, npend = 0, nsurv = 0, ncol = nL;  // entries [ncol, nL) still need their colour
-    // first step: the tile's cut (boxes in shared memory) instead of the root
-    const int ncut = *W.ncut;
-    for (int b0 = 0; b0 < ncut; b0 += 32) {
+    int sp = 0, nsurv = 0, ncol = nL;  // entries [ncol, nL) still need their colour
+    // first step: the tile's cut (at most 32 records in shared memory) instead of the root
+    {
+        const int ncut = *W.ncut;
         bool h = false;
         uint32_t rf = 0;
-        if (b0 + lane < ncut) {
-            const uint4 v = W.cut[b0 + lane];
-            float4 lo, hi;
-            child_of(v, lo, hi);
+        if (lane < ncut) {
+            const uint4 v = W.cut[lane];
             float te;
-            h = box_overlap(lo, hi, r, ta, tb, te);
+            h = record_hit(v, r, ta, tb, te);
             rf = v.w;
         }
-        const bool pi = h && !(rf & LEAF_BIT), pl = h && (rf & LEAF_BIT);
+        const bool leaf = (rf & LEAF_BIT) != 0;
+        const bool pi = h && !leaf, pl = h && leaf;
         const uint32_t bi = __ballot_sync(FULLMASK, pi), bl = __ballot_sync(FULLMASK, pl);
-        if (pi) W.stk[sp + __popc(bi & lt)] = rf;
-        if (pl) W.cand[npend + __popc(bl & lt)] = rf & ~LEAF_BIT;
-        sp += __popc(bi);
-        npend += __popc(bl);
+        if (pi) W.stk[__popc(bi & lt)] = rf;
+        if (pl) W.surv[__popc(bl & lt)] = rf & ~LEAF_BIT;
+        sp = __popc(bi);
+        nsurv = __popc(bl);
+        __syncwarp();
     }
-    __syncwarp();
-    while (sp > 0 || npend > 0 || nsurv > 0) {
+    while (sp > 0 || nsurv > 0) {
         if (sp > 0) {
-            // wide pops while the stack has room, then depth-first with a reserve
-            // (100 entries > the depth bound of the radix tree)
-            const int take = STK - sp >= 2 ? min(min(sp, 32), max((STK - 100 - sp) / 2, 1)) : 0;
+            const int take = pop_count(sp);
             if (take <= 0) {
                 if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
                 return 2;
@@ -286,68 +312,40 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
             const uint32_t ref = lane < take ? W.stk[base + lane] : 0u;
             __syncwarp();
             sp = base;
-            bool hl_ = false, hr_ = false;
-            uint32_t rl = 0, rr = 0;
+            uint32_t rf[4];
+            uint32_t hmask = 0, ni = 0, nl = 0;
             if (lane < take) {
                 cnt.visits++;
-                const uint4 vl = __ldg(P.nodeh + 2 * (size_t)ref), vr = __ldg(P.nodeh + 2 * (size_t)ref + 1);
-                float4 llo, lhi, rlo, rhi;
-                child_of(vl, llo, lhi);
-                child_of(vr, rlo, rhi);
-                float te;
-                hl_ = box_overlap(llo, lhi, r, ta, tb, te);
-                hr_ = box_overlap(rlo, rhi, r, ta, tb, te);
-                rl = vl.w;
-                rr = vr.w;
+                const uint4* nw = P.nodew + 4 * (size_t)ref;
+                uint4 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) v[j] = __ldg(nw + j);
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    float te;
+                    rf[j] = v[j].w;
+                    if (record_hit(v[j], r, ta, tb, te)) {
+                        hmask |= 1u << j;
+                        if (rf[j] & LEAF_BIT) nl++; else ni++;
+                    }
+                }
             }
-            const bool pl = hl_ && !(rl & LEAF_BIT), pr = hr_ && !(rr & LEAF_BIT);
-            const bool ll = hl_ && (rl & LEAF_BIT), lr = hr_ && (rr & LEAF_BIT);
-            const uint32_t bpl = __ballot_sync(FULLMASK, pl), bpr = __ballot_sync(FULLMASK, pr);
-            const uint32_t bll = __ballot_sync(FULLMASK, ll), blr = __ballot_sync(FULLMASK, lr);
-            const int po = sp + __popc(bpl & lt) + __popc(bpr & lt);
-            if (pr) W.stk[po] = rr;
-            if (pl) W.stk[po + (pr ? 1 : 0)] = rl;
-            const int co = npend + __popc(bll & lt) + __popc(blr & lt);
-            if (ll) W.cand[co] = rl & ~LEAF_BIT;
-            if (lr) W.cand[co + (ll ? 1 : 0)] = rr & ~LEAF_BIT;
-            sp += __popc(bpl) + __popc(bpr);
-            npend += __popc(bll) + __popc(blr);
-            __syncwarp();
-        }
-        // bounding-sphere test of queued candidates in full rounds (everything once
-        // the stack is empty); survivors are queued for the exact chord
-        int done = 0;
-        while (npend - done >= 32 || (sp == 0 && npend - done > 0)) {
-            const bool have = done + lane < npend;
-            uint32_t p = 0;
-            bool maybe = false;
-            if (have) {
-                const uint32_t leaf = W.cand[done + lane];
-                p = P.morton ? leaf : (uint32_t)P.perm[leaf];
-                const float4 sp4 = __ldg(&P.sph[p]);
-                const float vx = sp4.x - r.ox, vy = sp4.y - r.oy, vz = sp4.z - r.oz;
-                const float tp = vx * r.dx + vy * r.dy + vz * r.dz;
-                const float vv = vx * vx + vy * vy + vz * vz;
-                maybe = sp4.w > 0.0f && vv - tp * tp <= sp4.w * sp4.w + 4e-6f * vv && tp + sp4.w > ta &&
-                        tp - sp4.w < tb;
+            uint32_t tot;
+            const uint32_t ex = warp_excl_scan(ni | (nl << 16), tot);
+            int oi = sp + (int)(ex & 0xffffu), ol = nsurv + (int)(ex >> 16);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (hmask & (1u << j)) {
+                    if (rf[j] & LEAF_BIT) W.surv[ol++] = rf[j] & ~LEAF_BIT;
+                    else W.stk[oi++] = rf[j];
+                }
             }
-            const uint32_t bm = __ballot_sync(FULLMASK, maybe);
-            if (maybe) W.surv[nsurv + __popc(bm & lt)] = p;
-            nsurv += __popc(bm);
-            done = min(done + 32, npend);
+            sp += (int)(tot & 0xffffu);
+            nsurv += (int)(tot >> 16);
             __syncwarp();
         }
-        if (done > 0) {
-            // move the (< 32) leftover candidates to the front
-            const int left = npend - done;
-            const uint32_t v = lane < left ? W.cand[done + lane] : 0u;
-            __syncwarp();
-            if (lane < left) W.cand[lane] = v;
-            npend = left;
-            __syncwarp();
-        }
-        // exact chords of the sphere survivors, 32 at a time (all of them once
-        // the traversal has finished)
+        // exact chords of the queued leaves, 32 at a time (all of them once the
+        // traversal has finished)
         while (nsurv >= 32 || (sp == 0 && nsurv > 0)) {
             const int m = min(nsurv, 32);
             const bool h2 = lane < m;
@@ -389,49 +387,64 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
 }
 
 // ClosestHit(ta) = min over Gaussians whose chord has t_out > ta and t_in < tf of
-// max(t_in, ta); tf if there is none (Algorithm 1, Eq. 4).  Cooperative
-// traversal pruned by the warp's best value, near children on top of the stack.
-// Called with tf replaced by a smaller limit it returns the same minimum if one
-// lies below the limit, else the limit itself.
+// max(t_in, ta); tf if there is none (Algorithm 1, Eq. 4).  Cooperative 4-wide
+// traversal pruned by the warp's best value: a lane pushes its node's internal
+// children far to near (so the nearest is popped first) and queues leaves whose
+// box starts before the best value; after every step the queued leaves' exact
+// chords are solved 32 at a time and lower the best value.  Called with tf
+// replaced by a smaller limit it returns the same minimum if one lies below the
+// limit, else the limit itself.
+__device__ __forceinline__ void cswap_desc(float& ta_, uint32_t& ra, float& tb_, uint32_t& rb) {
+    if (ta_ < tb_) {
+        const float t = ta_; ta_ = tb_; tb_ = t;
+        const uint32_t x = ra; ra = rb; rb = x;
+    }
+}
+
 __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, float ta, float tf, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     if (lane == 0) cnt.chq++;
-    int sp = 0;
+    int sp = 0, nq = 0;
     float best = tf;
-    // first step: the tile's cut (boxes in shared memory) instead of the root
-    const int ncut = *W.ncut;
-    for (int b0 = 0; b0 < ncut; b0 += 32) {
+    // first step: the tile's cut (at most 32 records in shared memory) instead of the root
+    {
+        const int ncut = *W.ncut;
         bool h = false;
         uint32_t rf = 0;
-        float te = INFINITY, cand = INFINITY;
-        if (b0 + lane < ncut) {
-            const uint4 v = W.cut[b0 + lane];
-            float4 lo, hi;
-            child_of(v, lo, hi);
-            h = box_overlap(lo, hi, r, ta, tf, te);
+        float te = INFINITY;
+        if (lane < ncut) {
+            const uint4 v = W.cut[lane];
+            h = record_hit(v, r, ta, tf, te);
             rf = v.w;
-            if (h && (rf & LEAF_BIT)) {
-                const uint32_t leaf = rf & ~LEAF_BIT;
-                const int64_t p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
-                const Chord c = chord_of(P.geom, p, r);
+        }
+        const bool leaf = (rf & LEAF_BIT) != 0;
+        const bool pi = h && !leaf, pl = h && leaf;
+        const uint32_t bi = __ballot_sync(FULLMASK, pi), bl = __ballot_sync(FULLMASK, pl);
+        if (pi) {
+            W.stk[__popc(bi & lt)] = rf;
+            W.stkt[__popc(bi & lt)] = te;
+        }
+        if (pl) W.surv[__popc(bl & lt)] = rf & ~LEAF_BIT;
+        sp = __popc(bi);
+        nq = __popc(bl);
+        __syncwarp();
+    }
+    while (true) {
+        // exact chords of the queued leaves
+        while (nq > 0) {
+            const int m = min(nq, 32);
+            float cand = INFINITY;
+            if (lane < m) {
+                const Chord c = chord_of(P.geom, W.surv[nq - m + lane], r);
                 if (c.ok && c.tout > ta && c.tin < tf) cand = fmaxf(c.tin, ta);
             }
+            best = fminf(best, warp_min(cand));
+            nq -= m;
         }
-        best = fminf(best, warp_min(cand));
         if (best <= ta) return ta;
-        const bool pi = h && !(rf & LEAF_BIT) && te < best;
-        const uint32_t bi = __ballot_sync(FULLMASK, pi);
-        if (pi) {
-            const int o = sp + __popc(bi & lt);
-            W.stk[o] = rf;
-            W.stkt[o] = te;
-        }
-        sp += __popc(bi);
-    }
-    __syncwarp();
-    while (sp > 0) {
-        const int take = STK - sp >= 2 ? min(min(sp, 32), max((STK - 100 - sp) / 2, 1)) : 0;
+        if (sp == 0) break;
+        const int take = pop_count(sp);
         if (take <= 0) {
             if (lane == 0) atomicOr(P.status, (unsigned)RGX_ERR_STACK_OVERFLOW);
             return best;
@@ -441,47 +454,45 @@ __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, floa
         const float tent = lane < take ? W.stkt[base + lane] : INFINITY;
         __syncwarp();
         sp = base;
-        const bool active = lane < take && tent < best;
-        float cand = INFINITY;
-        bool hl_ = false, hr_ = false;
-        uint32_t rl = 0, rr = 0;
-        float tl = INFINITY, tr = INFINITY;
-        if (active) {
-            cnt.visits++;
-            const uint4 vl = __ldg(P.nodeh + 2 * (size_t)ref), vr = __ldg(P.nodeh + 2 * (size_t)ref + 1);
-            float4 llo, lhi, rlo, rhi;
-            child_of(vl, llo, lhi);
-            child_of(vr, rlo, rhi);
-            hl_ = box_overlap(llo, lhi, r, ta, best, tl);
-            hr_ = box_overlap(rlo, rhi, r, ta, best, tr);
-            rl = vl.w;
-            rr = vr.w;
+        float tt[4];
+        uint32_t rr[4];
+        uint32_t ni = 0, nl = 0, lmask = 0;
 #pragma unroll
-            for (int side = 0; side < 2; side++) {
-                const bool h = side ? hr_ : hl_;
-                const uint32_t rf = side ? rr : rl;
-                if (h && (rf & LEAF_BIT)) {
-                    const uint32_t leaf = rf & ~LEAF_BIT;
-                    const int64_t p = P.morton ? (int64_t)leaf : (int64_t)P.perm[leaf];
-                    const Chord c = chord_of(P.geom, p, r);
-                    if (c.ok && c.tout > ta && c.tin < tf) cand = fminf(cand, fmaxf(c.tin, ta));
+        for (int j = 0; j < 4; j++) { tt[j] = -INFINITY; rr[j] = 0u; }
+        if (lane < take && tent < best) {
+            cnt.visits++;
+            const uint4* nw = P.nodew + 4 * (size_t)ref;
+            uint4 v[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) v[j] = __ldg(nw + j);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float te;
+                if (record_hit(v[j], r, ta, best, te)) {
+                    rr[j] = v[j].w;
+                    if (v[j].w & LEAF_BIT) { lmask |= 1u << j; nl++; }
+                    else { tt[j] = te; ni++; }
                 }
             }
         }
-        best = fminf(best, warp_min(cand));
-        if (best <= ta) return ta;
-        // internal children still worth visiting, far one pushed first
-        bool pl = hl_ && !(rl & LEAF_BIT) && tl < best;
-        bool pr = hr_ && !(rr & LEAF_BIT) && tr < best;
-        const bool lnear = tl <= tr;
-        const bool p1 = lnear ? pr : pl, p2 = lnear ? pl : pr;   // p1 = far, p2 = near
-        const uint32_t r1 = lnear ? rr : rl, r2 = lnear ? rl : rr;
-        const float t1 = lnear ? tr : tl, t2 = lnear ? tl : tr;
-        const uint32_t b1 = __ballot_sync(FULLMASK, p1), b2 = __ballot_sync(FULLMASK, p2);
-        const int po = sp + __popc(b1 & lt) + __popc(b2 & lt);
-        if (p1) { W.stk[po] = r1; W.stkt[po] = t1; }
-        if (p2) { W.stk[po + (p1 ? 1 : 0)] = r2; W.stkt[po + (p1 ? 1 : 0)] = t2; }
-        sp += __popc(b1) + __popc(b2);
+        uint32_t ltot;
+        int ol = (int)warp_excl_scan(nl, ltot);
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (lmask & (1u << j)) W.surv[ol++] = rr[j] & ~LEAF_BIT;
+        nq = (int)ltot;
+        // internal children, far to near
+        cswap_desc(tt[0], rr[0], tt[1], rr[1]);
+        cswap_desc(tt[2], rr[2], tt[3], rr[3]);
+        cswap_desc(tt[0], rr[0], tt[2], rr[2]);
+        cswap_desc(tt[1], rr[1], tt[3], rr[3]);
+        cswap_desc(tt[1], rr[1], tt[2], rr[2]);
+        uint32_t tot;
+        const int o = sp + (int)warp_excl_scan(ni, tot);
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (j < (int)ni) { W.stk[o + j] = rr[j]; W.stkt[o + j] = tt[j]; }
+        sp += (int)tot;
         __syncwarp();
     }
     return best;
@@ -653,18 +664,20 @@ __device__ __forceinline__ float far_bound(const MarchParams& P, const rgx_camer
 
 template <int NS, bool BWD>
 __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const rgx_camera& C, int px, int py,
-                          Counters& cnt, float4& o_rgba, float4& o_state, int& o_nrec) {
+                          Counters& cnt, bool& whole, float4& o_rgba, float4& o_state, int& o_nrec) {
     const int lane = threadIdx.x & 31;
     const int k = lane % NS;
     const int cap = P.hit_cap;
     const Ray r = make_ray(C, px, py);
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Tf = 1.f, dTcoef = 0.f;
+    bool fwd_whole = false;  // adjoint: the forward marched this ray with a whole-ray first window
     if (BWD) {
         const float4 up = P.d_rgba[ray];
         if (up.x == 0.0f && up.y == 0.0f && up.z == 0.0f && up.w == 0.0f) return;
         a0 = up.x; a1 = up.y; a2 = up.z;
         const float4 st = P.state[ray];
-        Cf0 = st.x; Cf1 = st.y; Cf2 = st.z; Tf = st.w;
+        Cf0 = st.x; Cf1 = st.y; Cf2 = st.z; Tf = fabsf(st.w);
+        fwd_whole = signbit(st.w);
         dTcoef = (a0 * P.bg0 + a1 * P.bg1 + a2 * P.bg2 - up.w) * Tf;
     }
     // ---- bounds: t_n, and t_f = camera t_far or the exit of the scene box
@@ -689,9 +702,32 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
     int nrec = 0;
     int nL = 0;
     float w_lo = 1.0f, w_hi = 0.0f;  // current window (empty)
+    bool used_whole = false;
     float wlen = 4.0f * (float)NS * (uniform ? P.dt : P.dt_max);
     if (P.n > 0 && tf > tn && skip) {
-        const float th = w_closest(P, W, r, tn, tf, cnt);
+        // One window over the whole ray [t_n, t_f): when every chord fits in the
+        // list, ClosestHit(t_n) is its smallest max(t_in, t_n) (a chord outside the
+        // window would start later) and every later segment reuses the window.
+        // After an overflow the tile's remaining rays use the nearest-hit traversal.
+        float th = tf;
+        bool have = false;
+        if (BWD ? fwd_whole : whole) {
+            nL = 0;
+            if (lane == 0) cnt.windows++;
+            if (w_collect<BWD>(P, W, r, tn, tf, cap, nL, false, NoChunk(), cnt) == 0) {
+                have = true;
+                used_whole = true;
+                w_lo = tn;
+                w_hi = tf;
+                float m = INFINITY;
+                for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, tn));
+                th = fminf(warp_min(m), tf);
+            } else {
+                whole = false;
+                nL = 0;
+            }
+        }
+        if (!have) th = w_closest(P, W, r, tn, tf, cnt);
         if (uniform) {
             const int jj = (int)floorf((th - tn) / P.dt) - 1;
             j = jj > 0 ? jj : 0;
@@ -883,7 +919,8 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         if (lane == 0 && T != Tf) atomicOr(P.status, (unsigned)RGX_ERR_REPLAY);
     } else {
         o_rgba = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
-        o_state = make_float4(C0, C1, C2, T);
+        // the sign bit of T (>= 0) records the first-window path for the adjoint's replay
+        o_state = make_float4(C0, C1, C2, used_whole ? -T : T);
         o_nrec = nrec;
     }
 }
@@ -963,97 +1000,74 @@ __device__ __forceinline__ bool box_outside(const Frustum& F, float4 lo, float4 
     return false;
 }
 
-// The tile's BVH cut: a set of at most CUT child records (compressed box + ref)
-// whose subtrees hold every leaf whose box meets the view cone.  Starts from the
-// root's two children and replaces internal records by their children inside
-// the cone, level by level, while the set stays within CUT; records outside the
-// cone are dropped.  Every traversal of the tile's rays starts from it.
+// A 4-wide child record whose box lies entirely outside the view cone.
+__device__ __forceinline__ bool record_outside(const Frustum& F, uint4 v) {
+    float4 lo, hi;
+    child_of(v, lo, hi);
+    return box_outside(F, lo, hi);
+}
+
+// The tile's BVH cut: a set of at most CUT (= 32, one per lane) child records
+// whose subtrees hold every leaf whose bounds meet the view cone.  Starts from
+// the root's 4-wide record and replaces internal records by their children
+// inside the cone, level by level, while the set stays within CUT; records
+// outside the cone are dropped.  Every traversal of the tile's rays starts from it.
 #define CUT_LEVELS 48
-#define CUT_R (CUT / 32)
+static_assert(CUT == 32, "one cut record per lane");
 __device__ void build_cut(const MarchParams& P, const WS& W, const Frustum& F, Counters& cnt) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    bool keep = false;
-    if (lane < 2) {
-        v = __ldg(P.nodeh + lane);
-        float4 lo, hi;
-        child_of(v, lo, hi);
-        keep = !box_outside(F, lo, hi);
+    {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        bool keep = false;
+        if (lane < 4) {
+            v = __ldg(P.nodew + lane);
+            keep = !record_outside(F, v);
+        }
+        const uint32_t b = __ballot_sync(FULLMASK, keep);
+        if (keep) W.cut[__popc(b & lt)] = v;
+        if (lane == 0) *W.ncut = __popc(b);
+        __syncwarp();
     }
-    const uint32_t b = __ballot_sync(FULLMASK, keep);
-    if (keep) W.cut[__popc(b & lt)] = v;
-    int nc = __popc(b);
-    __syncwarp();
+    int nc = *W.ncut;
     for (int it = 0; it < CUT_LEVELS; it++) {
-        // record i = 32 j + lane
-        uint4 mine[CUT_R], c0[CUT_R], c1[CUT_R];
-        bool internal[CUT_R], k0[CUT_R], k1[CUT_R];
+        const bool have = lane < nc;
+        const uint4 mine = have ? W.cut[lane] : make_uint4(0u, 0u, 0u, LEAF_BIT);
+        const bool internal = have && !(mine.w & LEAF_BIT);
+        uint4 c[4];
+        bool k[4];
+        int kept = 0;
 #pragma unroll
-        for (int j = 0; j < CUT_R; j++) {
-            const int i = 32 * j + lane;
-            mine[j] = i < nc ? W.cut[i] : make_uint4(0u, 0u, 0u, LEAF_BIT);
-            internal[j] = i < nc && !(mine[j].w & LEAF_BIT);
-            c0[j] = make_uint4(0u, 0u, 0u, 0u);
-            c1[j] = c0[j];
-            k0[j] = k1[j] = false;
-            if (internal[j]) {
-                cnt.visits++;
-                c0[j] = __ldg(P.nodeh + 2 * (size_t)mine[j].w);
-                c1[j] = __ldg(P.nodeh + 2 * (size_t)mine[j].w + 1);
+        for (int j = 0; j < 4; j++) { c[j] = make_uint4(0u, 0u, 0u, 0u); k[j] = false; }
+        if (internal) {
+            cnt.visits++;
+#pragma unroll
+            for (int j = 0; j < 4; j++) c[j] = __ldg(P.nodew + 4 * (size_t)mine.w + j);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                k[j] = !record_outside(F, c[j]);
+                kept += k[j] ? 1 : 0;
             }
         }
         // a record grows the set by add = (children kept) - 1; shrinking ones always
         // expand, growing ones while the running total of growth (in record order) fits
-        bool expand[CUT_R];
-        bool anyx = false;
-        int run = 0;
-#pragma unroll
-        for (int j = 0; j < CUT_R; j++) {
-            if (internal[j]) {
-                float4 lo, hi;
-                child_of(c0[j], lo, hi);
-                k0[j] = !box_outside(F, lo, hi);
-                child_of(c1[j], lo, hi);
-                k1[j] = !box_outside(F, lo, hi);
-            }
-            const int add = internal[j] ? (int)k0[j] + (int)k1[j] - 1 : 0;
-            int pre = add > 0 ? add : 0;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(FULLMASK, pre, d);
-                if (lane >= d) pre += t;
-            }
-            expand[j] = internal[j] && (add <= 0 || nc + run + pre <= CUT);
-            run += __shfl_sync(FULLMASK, pre, 31);
-            anyx |= expand[j];
-        }
-        if (!__any_sync(FULLMASK, anyx)) break;
-        int off[CUT_R], mcount[CUT_R];
-        int total = 0;
-#pragma unroll
-        for (int j = 0; j < CUT_R; j++) {
-            mcount[j] = expand[j] ? (int)k0[j] + (int)k1[j] : (32 * j + lane < nc ? 1 : 0);
-            int o = mcount[j];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int t = __shfl_up_sync(FULLMASK, o, d);
-                if (lane >= d) o += t;
-            }
-            off[j] = total + o - mcount[j];
-            total += __shfl_sync(FULLMASK, o, 31);
-        }
+        const int add = internal ? kept - 1 : 0;
+        uint32_t gsum;
+        const int pre = (int)warp_excl_scan(add > 0 ? (uint32_t)add : 0u, gsum) + (add > 0 ? add : 0);
+        const bool expand = internal && (add <= 0 || nc + pre <= CUT);
+        if (!__any_sync(FULLMASK, expand)) break;
+        const int mcount = expand ? kept : (have ? 1 : 0);
+        uint32_t total;
+        int off = (int)warp_excl_scan((uint32_t)mcount, total);
         __syncwarp();
+        if (expand) {
 #pragma unroll
-        for (int j = 0; j < CUT_R; j++) {
-            if (expand[j]) {
-                if (k0[j]) W.cut[off[j]] = c0[j];
-                if (k1[j]) W.cut[off[j] + (k0[j] ? 1 : 0)] = c1[j];
-            } else if (32 * j + lane < nc) {
-                W.cut[off[j]] = mine[j];
-            }
+            for (int j = 0; j < 4; j++)
+                if (k[j]) W.cut[off++] = c[j];
+        } else if (have) {
+            W.cut[off] = mine;
         }
-        nc = total;
+        nc = (int)total;
         __syncwarp();
     }
     if (lane == 0) *W.ncut = nc;
@@ -1119,13 +1133,14 @@ __global__ void __launch_bounds__(RGX_BLOCK) k_march(MarchParams P) {
             }
             build_cut(P, W, tile_frustum(cam, pxa, pya, pxb, pyb), cnt);
         }
+        bool whole = true;  // whole-ray first windows, until one overflows
         for (int l = 0; l < 32; l++) {
             int px, py;
             if (!tile_pixel(cam, lt, l, zt, P.tile_w, P.tile_h, px, py)) continue;
             const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
             float4 o_rgba, o_state;
             int o_nrec = 0;
-            march_ray<NS, BWD>(P, W, ray, cam, px, py, cnt, o_rgba, o_state, o_nrec);
+            march_ray<NS, BWD>(P, W, ray, cam, px, py, cnt, whole, o_rgba, o_state, o_nrec);
             if (!BWD && lane == l) { my_rgba = o_rgba; my_state = o_state; my_nrec = o_nrec; }
         }
         if (!BWD) {
@@ -1259,7 +1274,7 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
                                int32_t* sched_n, cudaStream_t st) {
     MarchParams P;
     memset(&P, 0, sizeof P);
-    P.geom = s->geom; P.shc = s->shc; P.sph = s->sph; P.perm = s->perm; P.nodes = s->nodes; P.nodeh = s->nodeh; P.root = s->root;
+    P.geom = s->geom; P.shc = s->shc; P.sph = s->sph; P.perm = s->perm; P.nodes = s->nodes; P.nodew = s->nodew; P.root = s->root;
     P.n = s->n; P.morton = s->morton;
     P.cams = s->cams; P.ncam = ncam;
     P.flags = o->flags;
