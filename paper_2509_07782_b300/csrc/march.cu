@@ -91,9 +91,10 @@ struct WS {
     float2* tio;    // [cap] (t_in, t_out)
     float4* bg;     // [32]  (beta, gamma0..2)     adjoint only
     uint32_t* pid;  // [cap] packed index
-    uint32_t* seg;  // [cap] entries of the current segment
+    uint32_t* seg;  // [max(cap, STK)] entries of the current segment
     uint32_t* stk;  // [STK] node refs
-    float* stkt;    // [STK] entry distance (nearest-hit traversal)
+    float* stkt;    // [STK] entry distance (nearest-hit traversal); aliases seg, which
+                    // is dead whenever a traversal runs
     uint32_t* surv; // [SURV] leaves whose box meets the ray, awaiting the exact chord
     float* Y;       // [16] SH basis of the current ray direction
     uint4* cut;     // [CUT] the tile's BVH cut: compressed child records (box, ref)
@@ -101,7 +102,8 @@ struct WS {
 };
 
 __host__ __device__ inline size_t warp_bytes(int cap, bool bwd) {
-    size_t b = (size_t)cap * (16 + 16 + 8 + 4 + 4) + (size_t)STK * 8 + SURV * 4 + CUT * 16 + 16 * 4 + 16;
+    size_t b = (size_t)cap * (16 + 16 + 8 + 4) + (size_t)(cap > STK ? cap : STK) * 4 + (size_t)STK * 4 + SURV * 4 +
+               CUT * 16 + 16 * 4 + 16;
     if (bwd) b += (size_t)cap * (16 + 8) + 32 * 16;
     return (b + 15) & ~(size_t)15;
 }
@@ -116,9 +118,9 @@ __device__ inline WS carve(char* base, int cap, bool bwd) {
     else { w.acc = nullptr; w.bg = nullptr; }
     w.tio = (float2*)p; p += (size_t)cap * 8;
     if (bwd) { w.acc2 = (float2*)p; p += (size_t)cap * 8; } else w.acc2 = nullptr;
-    w.stkt = (float*)p; p += (size_t)STK * 4;
     w.pid = (uint32_t*)p; p += (size_t)cap * 4;
-    w.seg = (uint32_t*)p; p += (size_t)cap * 4;
+    w.seg = (uint32_t*)p; p += (size_t)(cap > STK ? cap : STK) * 4;
+    w.stkt = (float*)w.seg;
     w.stk = (uint32_t*)p; p += (size_t)STK * 4;
     w.surv = (uint32_t*)p; p += SURV * 4;
     w.Y = (float*)p; p += 16 * 4;
