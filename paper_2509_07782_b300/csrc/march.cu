@@ -203,24 +203,25 @@ __device__ __forceinline__ void local_frame(const float4* __restrict__ geom, int
 // SH colour c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_k); Y in shared memory.
 __device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_t p, const float* Y, float c[3]) {
     const float4* s = shc + 12 * p;
-    float r = 0.5f, g = 0.5f, b = 0.5f;
+    // two partial sums per channel (even / odd SH index) shorten the dependency chains
+    float r = 0.5f, g = 0.5f, b = 0.5f, r2 = 0.0f, g2 = 0.0f, b2 = 0.0f;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         // coefficients 12j .. 12j+11 = SH indices 4j .. 4j+3, three channels each
         const float4 v0 = __ldg(&s[3 * j]), v1 = __ldg(&s[3 * j + 1]), v2 = __ldg(&s[3 * j + 2]);
         const float4 y = *reinterpret_cast<const float4*>(Y + 4 * j);
         r += y.x * v0.x; g += y.x * v0.y; b += y.x * v0.z;
-        r += y.y * v0.w; g += y.y * v1.x; b += y.y * v1.y;
+        r2 += y.y * v0.w; g2 += y.y * v1.x; b2 += y.y * v1.y;
         r += y.z * v1.z; g += y.z * v1.w; b += y.z * v2.x;
-        r += y.w * v2.y; g += y.w * v2.z; b += y.w * v2.w;
+        r2 += y.w * v2.y; g2 += y.w * v2.z; b2 += y.w * v2.w;
     }
-    c[0] = fmaxf(r, 0.0f); c[1] = fmaxf(g, 0.0f); c[2] = fmaxf(b, 0.0f);
+    c[0] = fmaxf(r + r2, 0.0f); c[1] = fmaxf(g + g2, 0.0f); c[2] = fmaxf(b + b2, 0.0f);
 }
 
+// Minimum over the warp in one reduction: floats mapped to order-preserving
+// unsigned keys (no NaN reaches here).
 __device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULLMASK, v, o));
-    return v;
+    return ord2f(__reduce_min_sync(FULLMASK, f2ord(v)));
 }
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
@@ -315,7 +316,9 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
             __syncwarp();
             sp = base;
             uint32_t rf[4];
-            uint32_t hmask = 0, ni = 0, nl = 0;
+            bool hit[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) { rf[j] = 0u; hit[j] = false; }
             if (lane < take) {
                 cnt.visits++;
                 const uint4* nw = P.nodew + 4 * (size_t)ref;
@@ -326,24 +329,20 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
                 for (int j = 0; j < 4; j++) {
                     float te;
                     rf[j] = v[j].w;
-                    if (record_hit(v[j], r, ta, tb, te)) {
-                        hmask |= 1u << j;
-                        if (rf[j] & LEAF_BIT) nl++; else ni++;
-                    }
+                    hit[j] = record_hit(v[j], r, ta, tb, te);
                 }
             }
-            uint32_t tot;
-            const uint32_t ex = warp_excl_scan(ni | (nl << 16), tot);
-            int oi = sp + (int)(ex & 0xffffu), ol = nsurv + (int)(ex >> 16);
+            // slot-major compaction: internal children onto the stack, leaves into the queue
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                if (hmask & (1u << j)) {
-                    if (rf[j] & LEAF_BIT) W.surv[ol++] = rf[j] & ~LEAF_BIT;
-                    else W.stk[oi++] = rf[j];
-                }
+                const bool leaf = (rf[j] & LEAF_BIT) != 0;
+                const uint32_t bi = __ballot_sync(FULLMASK, hit[j] && !leaf);
+                const uint32_t bl = __ballot_sync(FULLMASK, hit[j] && leaf);
+                if (hit[j] && !leaf) W.stk[sp + __popc(bi & lt)] = rf[j];
+                if (hit[j] && leaf) W.surv[nsurv + __popc(bl & lt)] = rf[j] & ~LEAF_BIT;
+                sp += __popc(bi);
+                nsurv += __popc(bl);
             }
-            sp += (int)(tot & 0xffffu);
-            nsurv += (int)(tot >> 16);
             __syncwarp();
         }
         // exact chords of the queued leaves, 32 at a time (all of them once the
@@ -477,24 +476,31 @@ __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, floa
                 }
             }
         }
-        uint32_t ltot;
-        int ol = (int)warp_excl_scan(nl, ltot);
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            if (lmask & (1u << j)) W.surv[ol++] = rr[j] & ~LEAF_BIT;
-        nq = (int)ltot;
+        for (int j = 0; j < 4; j++) {
+            const bool q = (lmask >> j) & 1u;
+            const uint32_t bl = __ballot_sync(FULLMASK, q);
+            if (q) W.surv[nq + __popc(bl & lt)] = rr[j] & ~LEAF_BIT;
+            nq += __popc(bl);
+        }
         // internal children, far to near
         cswap_desc(tt[0], rr[0], tt[1], rr[1]);
         cswap_desc(tt[2], rr[2], tt[3], rr[3]);
         cswap_desc(tt[0], rr[0], tt[2], rr[2]);
         cswap_desc(tt[1], rr[1], tt[3], rr[3]);
         cswap_desc(tt[1], rr[1], tt[2], rr[2]);
-        uint32_t tot;
-        const int o = sp + (int)warp_excl_scan(ni, tot);
+        // slot-major: every lane's farthest child first, so the nearest ones end on top
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            if (j < (int)ni) { W.stk[o + j] = rr[j]; W.stkt[o + j] = tt[j]; }
-        sp += (int)tot;
+        for (int j = 0; j < 4; j++) {
+            const bool pu = j < (int)ni;
+            const uint32_t bi = __ballot_sync(FULLMASK, pu);
+            if (pu) {
+                const int o = sp + __popc(bi & lt);
+                W.stk[o] = rr[j];
+                W.stkt[o] = tt[j];
+            }
+            sp += __popc(bi);
+        }
         __syncwarp();
     }
     return best;
@@ -785,13 +791,21 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         int nexact = 0;
         if (!chunked) {
             const uint32_t lt = lanemask_lt();
-            for (int b = 0; b < nL; b += 32) {
-                const int e = b + lane;
-                bool in = false;
-                if (e < nL) { const float2 io = W.tio[e]; in = io.x < tcut && io.y > tS; }
-                const uint32_t bb = __ballot_sync(FULLMASK, in);
-                if (in) W.seg[nexact + __popc(bb & lt)] = (uint32_t)e;
-                nexact += __popc(bb);
+            // four 32-entry slices per step: all loads before the ballots
+            for (int b = 0; b < nL; b += 128) {
+                bool in[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int e = b + 32 * i + lane;
+                    in[i] = false;
+                    if (e < nL) { const float2 io = W.tio[e]; in[i] = io.x < tcut && io.y > tS; }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const uint32_t bb = __ballot_sync(FULLMASK, in[i]);
+                    if (in[i]) W.seg[nexact + __popc(bb & lt)] = (uint32_t)(b + 32 * i + lane);
+                    nexact += __popc(bb);
+                }
             }
             __syncwarp();
             if (nexact) eval_entries<NS>(W, true, nexact, tS, dtk, sig, S0, S1, S2);
