@@ -83,7 +83,7 @@ typedef struct {
     float sigma_eps;             /* truncation density: support is sigma(x) >= sigma_eps */
     float bg[3];                 /* background colour, added as T_final * bg */
     int32_t tile_w, tile_h;      /* ray tile, tile_w * tile_h == 32 (ZTILES only) */
-    int32_t hit_cap;             /* chord-list capacity per ray (multiple of 32, 32..512); never drops hits */
+    int32_t hit_cap;             /* chord-list capacity per ray (multiple of 32, 32..1024); never drops hits */
     int32_t max_segments;        /* loop bound per ray; 0 = derived from the ray length */
 } rgx_opts;
 
@@ -160,7 +160,7 @@ rgx_status rgx_render_backward(rgx_scene* scene, const rgx_camera* cams, int32_t
  * Autotuner for the open knobs of Algorithm 1 -- samples per segment N_S, the
  * capacity of the hit-primitive buffer H_b (hit_cap) -- and of the 2D ray
  * tiles of Sec. 3.3 (tile_w x tile_h, when RGX_ZTILES is set).  Each candidate
- * (4 tile shapes x hit_cap in {64,128,256,512} x N_S in {8,16,32} when
+ * (4 tile shapes x hit_cap in {128,192,256,384,512,640,768} x N_S in {8,16,32} when
  * tune_ns != 0, else base->n_s) is run once to warm up and twice timed with
  * CUDA events on `stream`, forward only or forward + adjoint
  * (with_backward != 0), on the caller's scene and cameras; the fastest

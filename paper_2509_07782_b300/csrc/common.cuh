@@ -31,7 +31,7 @@
 
 #define RGX_STACK 96          // >= depth of a radix tree over (63-bit code, 32-bit index) keys
 #define RGX_MAX_CAMS 1024
-#define RGX_BLOCK 64          // threads per block of the march kernels (2 warps)
+#define RGX_BLOCK 32          // threads per block of the march kernels (one warp: finest shared-memory granularity)
 
 // ---------------------------------------------------------------- scene
 struct rgx_scene {

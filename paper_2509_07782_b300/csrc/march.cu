@@ -171,14 +171,15 @@ __device__ __forceinline__ Chord chord_of(const float4* __restrict__ geom, int64
     const float ydy = g2.x * r.dx + g2.y * r.dy + g2.z * r.dz;
     const float ydz = g3.x * r.dx + g3.y * r.dy + g3.z * r.dz;
     c.a = ydx * ydx + ydy * ydy + ydz * ydz;
-    c.tc = -(y0x * ydx + y0y * ydy + y0z * ydz) / c.a;
+    const float inv_a = 1.0f / c.a;
+    c.tc = -(y0x * ydx + y0y * ydy + y0z * ydz) * inv_a;
     const float ycx = y0x + c.tc * ydx, ycy = y0y + c.tc * ydy, ycz = y0z + c.tc * ydz;
     c.qmin = ycx * ycx + ycy * ycy + ycz * ycz;
     c.Qe = g0.w;
     c.L = g1.w;
     const float rem = c.Qe - c.qmin;
     c.ok = (c.Qe > 0.0f) && (rem > 0.0f) && (c.a > 0.0f);
-    const float h = c.ok ? sqrtf(rem / c.a) : 0.0f;
+    const float h = c.ok ? sqrtf(rem * inv_a) : 0.0f;
     c.tin = c.tc - h;
     c.tout = c.tc + h;
     return c;
@@ -526,16 +527,18 @@ __device__ __forceinline__ void eval_entries(const WS& W, bool idx, int m, float
         float4 q4[4], c4[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) { q4[i] = W.q[e[i]]; c4[i] = W.c[e[i]]; }
+        float g[4];
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             const float u = __fmaf_rn((float)k, dtk, __fadd_rn(__fsub_rn(tS, q4[i].x), half));
             const float q = __fmaf_rn(__fmul_rn(q4[i].y, u), u, q4[i].z);
-            const float g = q <= q4[i].w ? exp2f(__fmaf_rn(q, NEG_HALF_LOG2E, c4[i].x)) : 0.0f;
-            sig = __fadd_rn(sig, g);
-            S0 = __fmaf_rn(g, c4[i].y, S0);
-            S1 = __fmaf_rn(g, c4[i].z, S1);
-            S2 = __fmaf_rn(g, c4[i].w, S2);
+            g[i] = q <= q4[i].w ? exp2f(__fmaf_rn(q, NEG_HALF_LOG2E, c4[i].x)) : 0.0f;
         }
+        // pairwise sums: two independent chains per accumulator
+        sig = __fadd_rn(sig, __fadd_rn(__fadd_rn(g[0], g[1]), __fadd_rn(g[2], g[3])));
+        S0 = __fadd_rn(S0, __fmaf_rn(g[0], c4[0].y, __fmaf_rn(g[1], c4[1].y, __fmaf_rn(g[2], c4[2].y, __fmul_rn(g[3], c4[3].y)))));
+        S1 = __fadd_rn(S1, __fmaf_rn(g[0], c4[0].z, __fmaf_rn(g[1], c4[1].z, __fmaf_rn(g[2], c4[2].z, __fmul_rn(g[3], c4[3].z)))));
+        S2 = __fadd_rn(S2, __fmaf_rn(g[0], c4[0].w, __fmaf_rn(g[1], c4[1].w, __fmaf_rn(g[2], c4[2].w, __fmul_rn(g[3], c4[3].w)))));
     }
     for (; h < m; h += G) {
         const uint32_t e = idx ? W.seg[h] : (uint32_t)h;
@@ -1091,7 +1094,7 @@ __device__ void build_cut(const MarchParams& P, const WS& W, const Frustum& F, C
 }
 
 template <int NS, bool BWD>
-__global__ void __launch_bounds__(RGX_BLOCK) k_march(MarchParams P) {
+__global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_tiles = (uint32_t*)smem;         // [ncam+1] tile prefix
     uint32_t* s_pix = s_tiles + (P.ncam + 1);    // [ncam+1] pixel prefix
@@ -1263,8 +1266,8 @@ static rgx_status check_opts(rgx_scene* s, const rgx_opts* o) {
     } else if (!(o->dt > 0.0f)) {
         return set_err(s, RGX_ERR_INVALID_ARG, "dt must be > 0");
     }
-    if (o->hit_cap < 32 || o->hit_cap > 512 || (o->hit_cap & 31))
-        return set_err(s, RGX_ERR_INVALID_ARG, "hit_cap must be a multiple of 32 in [32, 512]");
+    if (o->hit_cap < 32 || o->hit_cap > 1024 || (o->hit_cap & 31))
+        return set_err(s, RGX_ERR_INVALID_ARG, "hit_cap must be a multiple of 32 in [32, 1024]");
     if ((o->flags & RGX_ZTILES) && (o->tile_w <= 0 || o->tile_h <= 0 || o->tile_w * o->tile_h != 32))
         return set_err(s, RGX_ERR_INVALID_ARG, "tile_w * tile_h must be 32");
     if (!(o->t_eps >= 0.0f)) return set_err(s, RGX_ERR_INVALID_ARG, "t_eps must be >= 0");

@@ -32,7 +32,7 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
     float* const g[5] = {d_means, d_scales, d_quats, d_dens, d_sh};
     const int tiles[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
     const int ntiles = (base->flags & RGX_ZTILES) ? 4 : 1;
-    const int caps[6] = {128, 192, 256, 320, 384, 512};
+    const int caps[7] = {128, 192, 256, 384, 512, 640, 768};
     const int nss[3] = {8, 16, 32};
     const int nns = tune_ns ? 3 : 1;
     cudaEvent_t e0, e1;
@@ -42,7 +42,7 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
     rgx_opts bo = *base;
     rgx_status r = RGX_OK;
     for (int ti = 0; ti < ntiles && !r; ti++)
-        for (int ci = 0; ci < 6 && !r; ci++)
+        for (int ci = 0; ci < 7 && !r; ci++)
             for (int ni = 0; ni < nns && !r; ni++) {
                 rgx_opts o = *base;
                 if (ntiles > 1) { o.tile_w = tiles[ti][0]; o.tile_h = tiles[ti][1]; }
