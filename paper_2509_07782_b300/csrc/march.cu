@@ -27,11 +27,11 @@
 // The adjoint kernel replays exactly the same decisions and arithmetic, so it
 // reproduces T and the schedule bit for bit without storing any sample.  Per
 // segment it forms beta_k = dL/dsigma_k - gamma_k.c_k and gamma_k = dL/dc_k /
-// sigma_k from the residual C_final - C_<=k, then hit-parallel accumulates per
-// (ray, Gaussian) over all samples of the window sum w, sum w u, sum w u^2
-// (w = dL/dg g, u = t - t_c) and dL/dc_l; at the end of the window these give the
-// local-frame moments A0, V = sum w y, P = sum w y y^T that are added atomically
-// per Gaussian.  k_grad_finalize chains them to mu, s, q, sigma~ once per Gaussian.
+// sigma_k from the residual C_final - C_<=k, then hit-parallel sums per
+// (ray, Gaussian) over the segment's samples w, w u, w u^2 (w = dL/dg g,
+// u = t - t_c) and dL/dc_l; these give the local-frame moments A0, V = sum w y,
+// P = sum w y y^T that are added atomically per Gaussian right away.
+// k_grad_finalize chains them to mu, s, q, sigma~ once per Gaussian.
 #include <stdio.h>
 #include <cuda_fp16.h>
 #include "common.cuh"
@@ -86,8 +86,6 @@ struct Counters {
 struct WS {
     float4* q;      // [cap] (t_c, a, q_min, Q_eps)
     float4* c;      // [cap] (log2 sigma~, c0, c1, c2)
-    float4* acc;    // [cap] (A0, A1, A2, dc0)     adjoint only
-    float2* acc2;   // [cap] (dc1, dc2)            adjoint only
     float2* tio;    // [cap] (t_in, t_out)
     float4* bg;     // [32]  (beta, gamma0..2)     adjoint only
     uint32_t* pid;  // [cap] packed index
@@ -104,7 +102,7 @@ struct WS {
 __host__ __device__ inline size_t warp_bytes(int cap, bool bwd) {
     size_t b = (size_t)cap * (16 + 16 + 8 + 4) + (size_t)(cap > STK ? cap : STK) * 4 + (size_t)STK * 4 + SURV * 4 +
                CUT * 16 + 16 * 4 + 16;
-    if (bwd) b += (size_t)cap * (16 + 8) + 32 * 16;
+    if (bwd) b += 32 * 16;
     return (b + 15) & ~(size_t)15;
 }
 
@@ -114,10 +112,8 @@ __device__ inline WS carve(char* base, int cap, bool bwd) {
     w.q = (float4*)p; p += (size_t)cap * 16;
     w.c = (float4*)p; p += (size_t)cap * 16;
     w.cut = (uint4*)p; p += CUT * 16;
-    if (bwd) { w.acc = (float4*)p; p += (size_t)cap * 16; w.bg = (float4*)p; p += 32 * 16; }
-    else { w.acc = nullptr; w.bg = nullptr; }
+    if (bwd) { w.bg = (float4*)p; p += 32 * 16; } else w.bg = nullptr;
     w.tio = (float2*)p; p += (size_t)cap * 8;
-    if (bwd) { w.acc2 = (float2*)p; p += (size_t)cap * 8; } else w.acc2 = nullptr;
     w.pid = (uint32_t*)p; p += (size_t)cap * 4;
     w.seg = (uint32_t*)p; p += (size_t)(cap > STK ? cap : STK) * 4;
     w.stkt = (float*)w.seg;
@@ -374,10 +370,6 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
                 W.c[slot] = make_float4(ch.L, 0.f, 0.f, 0.f);
                 W.tio[slot] = make_float2(ch.tin, ch.tout);
                 W.pid[slot] = q;
-                if (BWD) {
-                    W.acc[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    W.acc2[slot] = make_float2(0.f, 0.f);
-                }
             }
             nL += nk;
             nsurv -= m;
@@ -557,10 +549,18 @@ __device__ __forceinline__ void eval_entries(const WS& W, bool idx, int m, float
     (void)base;
 }
 
-// Adjoint, hit-parallel: per entry, accumulate over the segment's samples
-// sum w, sum w u, sum w u^2 and dL/dc_l, with w = (beta_k + gamma_k . c_l) g.
+__device__ __forceinline__ void red_add4(float4* addr, float a, float b, float c, float d) {
+    atomicAdd(addr, make_float4(a, b, c, d));
+}
+
+// Adjoint, hit-parallel, one segment: per entry (lane = entry) the sums over the
+// segment's samples of w, w u, w u^2 (w = (beta_k + gamma_k . c_l) g, u = t - t_c)
+// and of dL/dc_l, turned at once into the local-frame moments A0, V = sum w y,
+// P = sum w y y^T and the SH gradients, which are added to the Gaussian's
+// accumulator (15 float4 atomics).  Nothing is kept per entry between segments.
 template <int NS>
-__device__ __forceinline__ void adjoint_entries(const WS& W, bool idx, int m, float tS, float dtk) {
+__device__ __forceinline__ void adjoint_flush(const MarchParams& P, const WS& W, const Ray& r, bool idx, int m,
+                                              float tS, float dtk) {
     const int lane = threadIdx.x & 31;
     const float half = __fmul_rn(0.5f, dtk);
     for (int h = lane; h < m; h += 32) {
@@ -583,31 +583,10 @@ __device__ __forceinline__ void adjoint_entries(const WS& W, bool idx, int m, fl
                 d0 += b.y * g; d1 += b.z * g; d2 += b.w * g;
             }
         }
-        float4 a = W.acc[e];
-        float2 a2 = W.acc2[e];
-        W.acc[e] = make_float4(a.x + A0, a.y + A1, a.z + A2, a.w + d0);
-        W.acc2[e] = make_float2(a2.x + d1, a2.y + d2);
-    }
-}
-
-__device__ __forceinline__ void red_add4(float4* addr, float a, float b, float c, float d) {
-    atomicAdd(addr, make_float4(a, b, c, d));
-}
-
-// Turn the accumulated per-(ray, Gaussian) sums of entries 0..m-1 into the
-// local-frame moments and add them (and the SH gradients) to the Gaussians.
-__device__ void flush_entries(const MarchParams& P, const WS& W, const Ray& r, int m) {
-    const float* Y = W.Y;
-    const int lane = threadIdx.x & 31;
-    for (int e = lane; e < m; e += 32) {
-        const float4 a = W.acc[e];
-        const float2 a2 = W.acc2[e];
-        if (a.x == 0.f && a.y == 0.f && a.z == 0.f && a.w == 0.f && a2.x == 0.f && a2.y == 0.f) continue;
+        if (A0 == 0.f && A1 == 0.f && A2 == 0.f && d0 == 0.f && d1 == 0.f && d2 == 0.f) continue;
         const int64_t p = W.pid[e];
-        const float4 q4 = W.q[e], c4 = W.c[e];
         float yc[3], yd[3];
         local_frame(P.geom, p, r, q4.x, yc, yd);
-        const float A0 = a.x, A1 = a.y, A2 = a.z;
         const float V0 = A0 * yc[0] + A1 * yd[0], V1 = A0 * yc[1] + A1 * yd[1], V2 = A0 * yc[2] + A1 * yd[2];
         float Pm[6];
         const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
@@ -621,13 +600,14 @@ __device__ void flush_entries(const MarchParams& P, const WS& W, const Ray& r, i
         red_add4(gp + 1, Pm[0], Pm[1], Pm[2], Pm[3]);
         red_add4(gp + 2, Pm[4], Pm[5], 0.f, 0.f);
         // SH: dL/dK_k = Y_k dL/dc_l where the colour is not clamped
-        const float m0 = c4.y > 0.f ? a.w : 0.f, m1 = c4.z > 0.f ? a2.x : 0.f, m2 = c4.w > 0.f ? a2.y : 0.f;
+        const float m0 = c4.y > 0.f ? d0 : 0.f, m1 = c4.z > 0.f ? d1 : 0.f, m2 = c4.w > 0.f ? d2 : 0.f;
+        const float* Y = W.Y;
 #pragma unroll
         for (int jx = 0; jx < 12; jx++) {
             float v[4];
 #pragma unroll
             for (int t = 0; t < 4; t++) {
-                const int idx = 4 * jx + t, k = idx / 3, ch = idx % 3;
+                const int ix = 4 * jx + t, k = ix / 3, ch = ix % 3;
                 v[t] = Y[k] * (ch == 0 ? m0 : (ch == 1 ? m1 : m2));
             }
             red_add4(gp + 4 + jx, v[0], v[1], v[2], v[3]);
@@ -769,7 +749,6 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         // ---- window of chords covering [tS, tcut)
         bool chunked = false;
         if (!(tS >= w_lo && tcut <= w_hi)) {
-            if (BWD) flush_entries(P, W, r, nL);
             const float need = te - tS;
             float len = fmaxf(wlen, need);
             while (true) {
@@ -913,13 +892,11 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
             if (lane < NS) W.bg[k] = valid ? make_float4(beta, g0, g1, g2) : make_float4(0.f, 0.f, 0.f, 0.f);
             __syncwarp();
             if (!chunked) {
-                adjoint_entries<NS>(W, true, nexact, tS, dtk);
+                adjoint_flush<NS>(P, W, r, true, nexact, tS, dtk);
                 __syncwarp();
             } else {
                 auto onfull2 = [&](int m) {
-                    adjoint_entries<NS>(W, false, m, tS, dtk);
-                    __syncwarp();
-                    flush_entries(P, W, r, m);
+                    adjoint_flush<NS>(P, W, r, false, m, tS, dtk);
                 };
                 nL = 0;
                 w_collect<BWD>(P, W, r, tS, tcut, cap, nL, true, onfull2, cnt);
@@ -934,7 +911,6 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         if (uniform) { j += NS; tS = __fmaf_rn((float)j, P.dt, tn); } else tS = te;
     }
     if (BWD) {
-        flush_entries(P, W, r, nL);
         if (lane == 0 && T != Tf) atomicOr(P.status, (unsigned)RGX_ERR_REPLAY);
     } else {
         o_rgba = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
