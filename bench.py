@@ -35,6 +35,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "torus_100k"
+# one-view forward + adjoint workloads (run_rgx) and their descriptions
+STEP_WORKLOADS = {
+    "torus_100k": "100,000 Gaussians on a noise-perturbed torus, one 800x800 view on a radius-4 orbit, BVH rebuild + "
+                  "forward + adjoint (skip + adaptive Eq.5 + Z-order + Z-tiles, N_S=16)",
+    "plain_2k": "2,000 Gaussians uniform in [-1,1]^3, one 64x64 view at radius 3, BVH rebuild + forward + adjoint "
+                "(uniform dt=0.01, no skipping, N_S=16)",
+    "outdoor_3m": "3,000,000 Gaussians (200-blob cluster + log-radius shell to r=100), one 1237x822 view from inside "
+                  "the cluster, BVH rebuild (63-bit codes) + forward + adjoint (skip + adaptive Eq.5 + Z-order + "
+                  "Z-tiles, N_S=16)",
+}
 METRIC = "Mrays/s render & fwd+bwd ms/iter vs plain marcher at ≤1e-4 err; % HBM peak"
 
 
@@ -50,9 +60,10 @@ def parse():
                    help="skip rgx_autotune (tile shape and hit_cap; N_S fixed) before the timed steps")
     p.add_argument("--tile", default=None, help="fixed ray-tile shape WxH (skips rgx_autotune)")
     p.add_argument("--hit-cap", type=int, default=None, help="fixed hit-list capacity (skips rgx_autotune)")
-    p.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_1m", "sweep_6m"],
-                   help="extra measurements: batch_1m = 8 uneven views, autotuned, CUDA-graph captured "
-                        "fwd+bwd; sweep_6m = 64 views forward, one persistent launch vs one launch per view")
+    p.add_argument("--workload", default=WORKLOAD, choices=list(STEP_WORKLOADS) + ["batch_1m", "sweep_6m"],
+                   help="torus_100k (default), plain_2k, outdoor_3m: one view, build + forward + adjoint; "
+                        "batch_1m = 8 uneven views, autotuned, CUDA-graph captured fwd+bwd; sweep_6m = 64 views "
+                        "forward, one persistent launch vs one launch per view")
     return p.parse_args()
 
 
@@ -138,7 +149,7 @@ def profiled_traffic(kernel: str):
 
 def launches_per_step(opts) -> int:
     passes = 8 if opts.morton63 else 4
-    build = 2 + 3 * passes + 1 + 2       # bounds, morton, sort passes, pack, karras + refit
+    build = 2 + 3 * passes + 1 + 3       # bounds, morton, sort passes, pack, karras + refit + widen
     return build + 1 + 2                  # forward march; backward march + finalize
 
 
@@ -175,11 +186,16 @@ def run_rgx(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(args.workload)
     if rank > 0:  # weak scaling: every rank renders its own seeded camera of the same scene
         cam0 = w.cameras[0]
         rng = np.random.Generator(np.random.PCG64(5000 + rank))
-        w.cameras = [synth.orbit_camera(rng, 4.0, cam0.width, cam0.height)]
+        if args.workload == "outdoor_3m":
+            w.cameras = [synth.inside_camera(rng, 0.3, cam0.width, cam0.height)]
+        elif args.workload == "plain_2k":
+            w.cameras = [synth.sphere_camera(rng, 3.0, cam0.width, cam0.height)]
+        else:
+            w.cameras = [synth.orbit_camera(rng, 4.0, cam0.width, cam0.height)]
     opts = rgx.make_opts(w.options)
     cams = rgx.Cameras(w.cameras)
     R = cams.n_rays
@@ -293,8 +309,8 @@ def run_rgx(args, rank, world, local):
     # caller-order storage, scanline rays): forward and forward+adjoint
     plain = None
     if not args.no_plain:
-        po = synth.Options(dt=w.options.dt_min, n_s=w.options.n_s, sigma_eps=w.options.sigma_eps,
-                           hit_cap=w.options.hit_cap)
+        po = synth.Options(dt=w.options.dt_min if w.options.adaptive else w.options.dt, n_s=w.options.n_s,
+                           sigma_eps=w.options.sigma_eps, hit_cap=w.options.hit_cap, morton63=w.options.morton63)
         popts = rgx.make_opts(po)
         sp = rgx.Scene(local)
         for _ in range(2):
@@ -317,7 +333,7 @@ def run_rgx(args, rank, world, local):
             flush.fill_(0.0)
         plain = {"fwd_ms": statistics.median(fm), "bwd_ms": statistics.median(fb),
                  "render_mrays_s": R / statistics.median(fm) / 1e3,
-                 "options": "uniform dt=0.005, N_S=16, no skip, caller order, scanline rays"}
+                 "options": f"uniform dt={po.dt}, N_S={po.n_s}, no skip, caller order, scanline rays"}
         if sp.status() != 0:
             plain["status"] = "device status nonzero"
 
@@ -336,12 +352,12 @@ def run_rgx(args, rank, world, local):
                 n=w.scene.n, steps_launches=launches_per_step(w.options) * args.steps)
 
 
-def cpu_baseline(max_seconds=12.0, npix_start=256):
+def cpu_baseline(workload=WORKLOAD, max_seconds=12.0, npix_start=256):
     """FP64 oracle (as it stands) on the host cores: forward + adjoint on a
     seeded pixel sample of the same view, grown until ~max_seconds."""
     import oracle
     from paper_2509_07782_b300 import synth
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(workload)
     cam = w.cameras[0]
     P = oracle.Params(w.scene)
     cores = os.cpu_count() or 1
@@ -357,7 +373,8 @@ def cpu_baseline(max_seconds=12.0, npix_start=256):
             break
         npix = min(cam.n_rays, npix * 4)
     return {"value": len(pix) / dt / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-            "sample": f"{len(pix)} seeded pixels of the 800x800 view, forward + adjoint, {dt:.2f} s"}
+            "sample": f"{len(pix)} seeded pixels of the {cam.width}x{cam.height} view, forward + adjoint, "
+                      f"{dt:.2f} s"}
 
 
 def run_batch(args):
@@ -463,7 +480,7 @@ def run_sweep(args):
 def main():
     args = parse()
     rank, world, local = dist_env()
-    if args.workload != WORKLOAD and args.impl != "reference":
+    if args.workload not in STEP_WORKLOADS and args.impl != "reference":
         if rank == 0:
             print(json.dumps(run_batch(args) if args.workload == "batch_1m" else run_sweep(args)))
         return
@@ -472,30 +489,36 @@ def main():
             return
         import oracle
         from paper_2509_07782_b300 import synth
-        w = synth.workload(WORKLOAD)
+        w = synth.workload(args.workload)
         cam = w.cameras[0]
         P = oracle.Params(w.scene)
         cores = os.cpu_count() or 1
-        pix = synth.pixel_subset(cam, 2048, seed=3)
+        # the oracle brute-forces every Gaussian per ray: the sample shrinks with N
+        npix = int(min(2048, max(64, 2048 * 100_000 // max(w.scene.n, 1))))
+        pix = synth.pixel_subset(cam, min(npix, cam.n_rays), seed=3)
+        with_bwd = args.workload != "sweep_6m"
         W = np.random.default_rng(4).normal(size=(len(pix), 4))
         for _ in range(max(args.warmup, 0)):
-            oracle.render(w.scene, cam, w.options, pix=pix[:64], params=P, nthreads=cores)
+            oracle.render(w.scene, cam, w.options, pix=pix[:16], params=P, nthreads=cores)
         times = []
         for _ in range(args.steps):
             t0 = time.perf_counter()
             oracle.render(w.scene, cam, w.options, pix=pix, params=P, nthreads=cores)
-            oracle.backward(w.scene, cam, w.options, W, pix=pix, params=P, nthreads=cores)
+            if with_bwd:
+                oracle.backward(w.scene, cam, w.options, W, pix=pix, params=P, nthreads=cores)
             times.append(time.perf_counter() - t0)
         tot = sum(times)
         v = len(pix) * args.steps / tot / 1e6
         out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mrays/s", "n_gpus": args.gpus,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "config": {"workload": f"{WORKLOAD}: 100k Gaussians, 800x800 view, "
-                                               "forward + adjoint, skip + adaptive + Z-order",
-                                               "sample": f"{len(pix)} seeded pixels per step"},
+               "data": "synthetic",
+               "config": {"workload": f"{args.workload}: " + STEP_WORKLOADS.get(
+                   args.workload, f"{w.scene.n} Gaussians, first of {len(w.cameras)} views"),
+                          "sample": f"{len(pix)} seeded pixels of the {cam.width}x{cam.height} view per step"},
                "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{len(pix)} seeded pixels per step, forward + adjoint"},
+                                "sample": f"{len(pix)} seeded pixels per step, forward"
+                                          + (" + adjoint" if with_bwd else "")},
                "e2e": {"value": v, "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
         return
@@ -532,9 +555,8 @@ def main():
         "metric": METRIC, "value": r["value"], "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: {r['n']} Gaussians on a torus, one 800x800 view, BVH rebuild + "
-                               "forward + adjoint (skip + adaptive Eq.5 + Z-order + Z-tiles, N_S=16; tile shape "
-                               "and hit_cap from rgx_autotune unless --no-tune)",
+        "config": {"workload": f"{args.workload}: " + STEP_WORKLOADS[args.workload] +
+                               " (tile shape and hit_cap from rgx_autotune unless fixed)",
                    "rays_per_step_per_gpu": r["R"], "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"{world} independent views, no data-path collective",
                    "autotuned": r["tuned"]},
@@ -550,7 +572,7 @@ def main():
         "device_status": r["status"],
     }
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(out))
 
 
