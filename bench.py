@@ -178,6 +178,39 @@ def alu_model(evals, hits, segs, rays, ns, backward: bool):
     return evals * per_eval + hits * per_hit
 
 
+def rank_workload(name: str, rank: int):
+    """The workload as rank `rank` renders it: rank 0 the named view, every other
+    rank its own seeded view of the same scene (weak scaling, nothing shared on
+    the data path)."""
+    from paper_2509_07782_b300 import synth
+    w = synth.workload(name)
+    if rank > 0:
+        cam0 = w.cameras[0]
+        rng = np.random.Generator(np.random.PCG64(5000 + rank))
+        if name == "outdoor_3m":
+            w.cameras = [synth.inside_camera(rng, 0.3, cam0.width, cam0.height)]
+        elif name == "plain_2k":
+            w.cameras = [synth.sphere_camera(rng, 3.0, cam0.width, cam0.height)]
+        else:
+            w.cameras = [synth.orbit_camera(rng, 4.0, cam0.width, cam0.height)]
+    return w
+
+
+def max_over_ranks(values, world: int, device=None):
+    """Element-wise maximum of per-rank timings (ms) over all ranks."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def whole_job_mrays(world: int, rays_per_rank: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: rays of all ranks over the slowest rank's time."""
+    return world * rays_per_rank * steps / (total_ms / 1e3) / 1e6
+
+
 def run_rgx(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -186,16 +219,7 @@ def run_rgx(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = synth.workload(args.workload)
-    if rank > 0:  # weak scaling: every rank renders its own seeded camera of the same scene
-        cam0 = w.cameras[0]
-        rng = np.random.Generator(np.random.PCG64(5000 + rank))
-        if args.workload == "outdoor_3m":
-            w.cameras = [synth.inside_camera(rng, 0.3, cam0.width, cam0.height)]
-        elif args.workload == "plain_2k":
-            w.cameras = [synth.sphere_camera(rng, 3.0, cam0.width, cam0.height)]
-        else:
-            w.cameras = [synth.orbit_camera(rng, 4.0, cam0.width, cam0.height)]
+    w = rank_workload(args.workload, rank)
     opts = rgx.make_opts(w.options)
     cams = rgx.Cameras(w.cameras)
     R = cams.n_rays
@@ -337,16 +361,12 @@ def run_rgx(args, rank, world, local):
         if sp.status() != 0:
             plain["status"] = "device status nonzero"
 
-    # max over ranks
-    vals = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    total_ms, e2e_ms = float(vals[0]), float(vals[1])
+    total_ms, e2e_ms = max_over_ranks([total_ms, e2e_ms], world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * R * args.steps / (total_ms / 1e3) / 1e6
+    value = whole_job_mrays(world, R, args.steps, total_ms)
     return dict(R=R, ms_per_step=ms_per_step, value=value, build_ms=statistics.median(build_ms),
                 fwd_ms=statistics.median(fwd_ms), bwd_ms=statistics.median(bwd_ms), wall_s=wall,
-                e2e=dict(value=world * R / (e2e_ms / 1e3) / 1e6, unit="Mrays/s", h2d_bytes_per_step=h2d,
+                e2e=dict(value=whole_job_mrays(world, R, 1, e2e_ms), unit="Mrays/s", h2d_bytes_per_step=h2d,
                          d2h_bytes_per_step=d2h, ms_per_step=e2e_ms),
                 counters_fwd=cf, counters_bwd=cb, clocks=clocks, status=st, plain=plain, opts=w.options, tuned=tuned,
                 n=w.scene.n, steps_launches=launches_per_step(w.options) * args.steps)
