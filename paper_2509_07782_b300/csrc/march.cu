@@ -638,12 +638,10 @@ __device__ __forceinline__ Ray make_ray(const rgx_camera& C, int px, int py) {
 
 // t_f: the camera's t_far, or (t_far <= 0) the exit of the scene box (t_n when
 // the ray misses the box).
-__device__ __forceinline__ float far_bound(const MarchParams& P, const rgx_camera& C, const Ray& r) {
+__device__ __forceinline__ float far_bound(const float4& lo, const float4& hi, const rgx_camera& C, const Ray& r) {
     const float tn = C.t_near;
     float tf = C.t_far;
     if (!(tf > 0.0f)) {
-        const float4 lo = make_float4(P.root[0], P.root[1], P.root[2], 0.f);
-        const float4 hi = make_float4(P.root[3], P.root[4], P.root[5], 0.f);
         float tentry;
         const bool in = box_overlap(lo, hi, r, -INFINITY, INFINITY, tentry);
         const float fx = r.ix >= 0.0f ? hi.x : lo.x, fy = r.iy >= 0.0f ? hi.y : lo.y, fz = r.iz >= 0.0f ? hi.z : lo.z;
@@ -655,6 +653,7 @@ __device__ __forceinline__ float far_bound(const MarchParams& P, const rgx_camer
 
 template <int NS, bool BWD>
 __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const rgx_camera& C, int px, int py,
+                          const float4& root_lo, const float4& root_hi, const float4& up, const float4& st,
                           Counters& cnt, bool& whole, float4& o_rgba, float4& o_state, int& o_nrec) {
     const int lane = threadIdx.x & 31;
     const int k = lane % NS;
@@ -663,17 +662,15 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
     float a0 = 0.f, a1 = 0.f, a2 = 0.f, Cf0 = 0.f, Cf1 = 0.f, Cf2 = 0.f, Tf = 1.f, dTcoef = 0.f;
     bool fwd_whole = false;  // adjoint: the forward marched this ray with a whole-ray first window
     if (BWD) {
-        const float4 up = P.d_rgba[ray];
         if (up.x == 0.0f && up.y == 0.0f && up.z == 0.0f && up.w == 0.0f) return;
         a0 = up.x; a1 = up.y; a2 = up.z;
-        const float4 st = P.state[ray];
         Cf0 = st.x; Cf1 = st.y; Cf2 = st.z; Tf = fabsf(st.w);
         fwd_whole = signbit(st.w);
         dTcoef = (a0 * P.bg0 + a1 * P.bg1 + a2 * P.bg2 - up.w) * Tf;
     }
     // ---- bounds: t_n, and t_f = camera t_far or the exit of the scene box
     const float tn = C.t_near;
-    const float tf = far_bound(P, C, r);
+    const float tf = far_bound(root_lo, root_hi, C, r);
     {
         float Y[16];
         sh_basis16(r.dx, r.dy, r.dz, Y);
@@ -1089,6 +1086,9 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
     }
     __syncthreads();
     const uint32_t total = s_tiles[P.ncam];
+    // the scene box (t_f of every ray), in registers for the whole launch
+    const float4 root_lo = make_float4(P.root[0], P.root[1], P.root[2], 0.f);
+    const float4 root_hi = make_float4(P.root[3], P.root[4], P.root[5], 0.f);
     while (true) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(P.queue, 1u);
@@ -1097,19 +1097,23 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
         int lo = 0, hi = P.ncam;
         while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (s_tiles[mid] <= t) lo = mid; else hi = mid; }
         const int c = lo;
-        const rgx_camera& cam = P.cams[c];
+        const rgx_camera cam = P.cams[c];  // in registers for the tile's 32 rays
         const uint32_t lt = t - s_tiles[c];
         Counters cnt = {0, 0, 0, 0, 0, 0, 0};
         float4 my_rgba = make_float4(0.f, 0.f, 0.f, 0.f), my_state = my_rgba;
         int my_nrec = 0;
         bool work = P.n > 0;
+        // adjoint: lane l holds the upstream gradient and forward state of the tile's ray l
+        float4 my_up = make_float4(0.f, 0.f, 0.f, 0.f), my_st = my_up;
         if (BWD && work) {
             // the adjoint skips tiles whose rays all have a zero upstream gradient
             int px, py;
             bool nz = false;
             if (tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
-                const float4 up = P.d_rgba[(int64_t)s_pix[c] + (int64_t)py * cam.width + px];
-                nz = up.x != 0.0f || up.y != 0.0f || up.z != 0.0f || up.w != 0.0f;
+                const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
+                my_up = P.d_rgba[ray];
+                my_st = P.state[ray];
+                nz = my_up.x != 0.0f || my_up.y != 0.0f || my_up.z != 0.0f || my_up.w != 0.0f;
             }
             work = __any_sync(FULLMASK, nz);
         }
@@ -1135,7 +1139,15 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
             const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
             float4 o_rgba, o_state;
             int o_nrec = 0;
-            march_ray<NS, BWD>(P, W, ray, cam, px, py, cnt, whole, o_rgba, o_state, o_nrec);
+            float4 up_l = make_float4(0.f, 0.f, 0.f, 0.f), st_l = up_l;
+            if (BWD) {
+                up_l = make_float4(__shfl_sync(FULLMASK, my_up.x, l), __shfl_sync(FULLMASK, my_up.y, l),
+                                   __shfl_sync(FULLMASK, my_up.z, l), __shfl_sync(FULLMASK, my_up.w, l));
+                st_l = make_float4(__shfl_sync(FULLMASK, my_st.x, l), __shfl_sync(FULLMASK, my_st.y, l),
+                                   __shfl_sync(FULLMASK, my_st.z, l), __shfl_sync(FULLMASK, my_st.w, l));
+            }
+            march_ray<NS, BWD>(P, W, ray, cam, px, py, root_lo, root_hi, up_l, st_l, cnt, whole, o_rgba, o_state,
+                               o_nrec);
             if (!BWD && lane == l) { my_rgba = o_rgba; my_state = o_state; my_nrec = o_nrec; }
         }
         if (!BWD) {
