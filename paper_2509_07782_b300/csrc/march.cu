@@ -61,6 +61,7 @@ struct MarchParams {
     float dt, dt_min, dt_max, beta, t_eps;
     float bg0, bg1, bg2;
     int tile_w, tile_h, hit_cap, max_segments;
+    uint32_t min_items;  // small views are split until they have this many work items (16 per SM)
     float4* rgba;
     float4* state;
     const float4* d_rgba;
@@ -696,7 +697,8 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         // One window over the whole ray [t_n, t_f): when every chord fits in the
         // list, ClosestHit(t_n) is its smallest max(t_in, t_n) (a chord outside the
         // window would start later) and every later segment reuses the window.
-        // After an overflow the tile's remaining rays use the nearest-hit traversal.
+        // After an overflow the work item's remaining rays use the nearest-hit
+        // traversal.
         float th = tf;
         bool have = false;
         if (BWD ? fwd_whole : whole) {
@@ -1069,18 +1071,26 @@ __device__ void build_cut(const MarchParams& P, const WS& W, const Frustum& F, C
 template <int NS, bool BWD>
 __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t* s_tiles = (uint32_t*)smem;         // [ncam+1] tile prefix
+    uint32_t* s_tiles = (uint32_t*)smem;         // [ncam+1] work-item prefix
     uint32_t* s_pix = s_tiles + (P.ncam + 1);    // [ncam+1] pixel prefix
-    const size_t head = ((size_t)(2 * (P.ncam + 1)) * 4 + 15) & ~(size_t)15;
+    uint32_t* s_shift = s_pix + (P.ncam + 1);    // [ncam+1] per camera: a work item is 32 >> shift rays
+    const size_t head = ((size_t)(3 * (P.ncam + 1)) * 4 + 15) & ~(size_t)15;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WS W = carve((char*)smem + head + (size_t)warp * warp_bytes(P.hit_cap, BWD), P.hit_cap, BWD);
     const bool zt = (P.flags & RGX_ZTILES) != 0;
     if (threadIdx.x == 0) {
         uint32_t tsum = 0, psum = 0;
         for (int c = 0; c < P.ncam; c++) {
+            // a small view is split into smaller work items until it has 16 per SM (about
+            // two per resident warp); the split depends on the view and the device alone,
+            // so a view renders the same in any batch
+            const uint32_t rays = (uint32_t)(P.cams[c].width * P.cams[c].height);
+            uint32_t sh = 0;
+            while (sh < 5 && rays / (32u >> sh) < P.min_items) sh++;
+            s_shift[c] = sh;
             s_tiles[c] = tsum; s_pix[c] = psum;
-            tsum += tiles_of(P.cams[c], zt, P.tile_w, P.tile_h);
-            psum += (uint32_t)(P.cams[c].width * P.cams[c].height);
+            tsum += tiles_of(P.cams[c], zt, P.tile_w, P.tile_h) << sh;
+            psum += rays;
         }
         s_tiles[P.ncam] = tsum; s_pix[P.ncam] = psum;
     }
@@ -1098,7 +1108,11 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
         while (hi - lo > 1) { const int mid = (lo + hi) >> 1; if (s_tiles[mid] <= t) lo = mid; else hi = mid; }
         const int c = lo;
         const rgx_camera cam = P.cams[c];  // in registers for the tile's 32 rays
-        const uint32_t lt = t - s_tiles[c];
+        const uint32_t item = t - s_tiles[c], sh = s_shift[c];
+        const uint32_t lt = item >> sh;                        // the tile
+        const int l0 = (int)(item & ((1u << sh) - 1u)) << (5 - sh);
+        const int l1 = l0 + (32 >> sh);                        // its rays [l0, l1)
+        const bool mine = lane >= l0 && lane < l1;
         Counters cnt = {0, 0, 0, 0, 0, 0, 0};
         float4 my_rgba = make_float4(0.f, 0.f, 0.f, 0.f), my_state = my_rgba;
         int my_nrec = 0;
@@ -1109,7 +1123,7 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
             // the adjoint skips tiles whose rays all have a zero upstream gradient
             int px, py;
             bool nz = false;
-            if (tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
+            if (mine && tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
                 const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
                 my_up = P.d_rgba[ray];
                 my_st = P.state[ray];
@@ -1132,8 +1146,8 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
             }
             build_cut(P, W, tile_frustum(cam, pxa, pya, pxb, pyb), cnt);
         }
-        bool whole = true;  // whole-ray first windows, until one overflows
-        for (int l = 0; l < 32; l++) {
+        bool whole = true;  // whole-ray first windows, until one overflows in this work item
+        for (int l = l0; l < l1; l++) {
             int px, py;
             if (!tile_pixel(cam, lt, l, zt, P.tile_w, P.tile_h, px, py)) continue;
             const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
@@ -1152,7 +1166,7 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
         }
         if (!BWD) {
             int px, py;
-            if (tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
+            if (mine && tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
                 const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
                 P.rgba[ray] = my_rgba;
                 if (P.state) P.state[ray] = my_state;
@@ -1163,7 +1177,7 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
             int nvalid = 0;
             {
                 int px, py;
-                nvalid = tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py) ? 1 : 0;
+                nvalid = mine && tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py) ? 1 : 0;
             }
             const unsigned v[8] = {(unsigned)nvalid, cnt.segs, cnt.hits, cnt.evals, cnt.visits, cnt.chq, cnt.skips,
                                    cnt.windows};
@@ -1293,11 +1307,12 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     P.d_rgba = (const float4*)d_rgba; P.grad = s->grad;
     P.sched = (float2*)sched; P.sched_cap = sched_cap; P.sched_n = sched_n;
     P.queue = s->queue; P.status = s->status; P.counters = s->counters;
+    P.min_items = 16u * (uint32_t)s->num_sms;
     RGX_CUDA(s, cudaMemcpyAsync(s->cams, cams, sizeof(rgx_camera) * ncam, cudaMemcpyHostToDevice, st));
     RGX_CUDA(s, cudaMemsetAsync(s->queue, 0, sizeof(unsigned), st));
     RGX_CUDA(s, cudaMemsetAsync(s->counters, 0, 8 * sizeof(unsigned long long), st));
     void* k = pick_kernel(o->n_s, bwd);
-    const size_t head = ((size_t)(2 * (ncam + 1)) * 4 + 15) & ~(size_t)15;
+    const size_t head = ((size_t)(3 * (ncam + 1)) * 4 + 15) & ~(size_t)15;
     const size_t smem = head + (size_t)WARPS * warp_bytes(o->hit_cap, bwd);
     int occ = 0;
     for (int i = 0; i < s->ncfg; i++)
@@ -1311,6 +1326,7 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     }
     if (occ < 1) occ = 1;
     const int grid = s->num_sms * occ;
+
     void* args[] = {&P};
     RGX_CUDA(s, cudaLaunchKernel(k, dim3(grid), dim3(RGX_BLOCK), args, smem, st));
     return RGX_OK;
