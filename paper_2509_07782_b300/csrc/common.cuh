@@ -62,6 +62,8 @@ struct rgx_scene {
     float* root = nullptr;         // [8] scene box
     float4* grad = nullptr;        // [16n] backward accumulators (packed order)
     int64_t grad_cap = 0;
+    float4* spill = nullptr;       // adjoint scratch: chunk entries of overflowing segments, per resident warp
+    size_t spill_cap = 0;          // in float4
     // render
     rgx_camera* cams = nullptr; int cams_cap = 0;
     unsigned int* queue = nullptr; // [4] persistent work counters

@@ -44,6 +44,7 @@
 #define STK_RES 152                                 // depth-first reserve: 3 x (4-wide depth bound 48) + 4
 #define SURV 160                                    // leaves awaiting their exact chord (< 32 left + 128 new)
 #define CUT 32                                      // child records of a tile's BVH cut
+#define SPILL_CAP 4096                              // adjoint: chunk entries kept per warp in global scratch
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -66,6 +67,7 @@ struct MarchParams {
     float4* state;
     const float4* d_rgba;
     float4* grad;
+    float4* spill;  // adjoint: [grid][SPILL_CAP][3] chunk entries (q, c, pid) of an overflowing segment
     float2* sched;
     int sched_cap;
     int32_t* sched_n;
@@ -747,6 +749,9 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         const float tcut = fminf(te, tf);
         // ---- window of chords covering [tS, tcut)
         bool chunked = false;
+        bool spill_ok = BWD && P.spill != nullptr;  // adjoint: chunks kept in this warp's scratch
+        float4* wspill = BWD && P.spill
+            ? P.spill + ((size_t)blockIdx.x * WARPS + (threadIdx.x >> 5)) * SPILL_CAP * 3 : nullptr;
         if (!(tS >= w_lo && tcut <= w_hi)) {
             const float need = te - tS;
             float len = fmaxf(wlen, need);
@@ -794,6 +799,19 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
             int tot = 0;
             auto onfull = [&](int m) {
                 eval_entries<NS>(W, false, m, tS, dtk, sig, S0, S1, S2);
+                if (BWD && spill_ok) {
+                    // keep the chunk for the adjoint pass (no second traversal)
+                    if (tot + m <= SPILL_CAP) {
+                        for (int e = lane; e < m; e += 32) {
+                            float4* d = wspill + 3 * (size_t)(tot + e);
+                            d[0] = W.q[e];
+                            d[1] = W.c[e];
+                            d[2] = make_float4(__uint_as_float(W.pid[e]), 0.f, 0.f, 0.f);
+                        }
+                    } else {
+                        spill_ok = false;
+                    }
+                }
                 tot += m;
                 __syncwarp();
             };
@@ -893,6 +911,19 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
             if (!chunked) {
                 adjoint_flush<NS>(P, W, r, true, nexact, tS, dtk);
                 __syncwarp();
+            } else if (spill_ok) {
+                // the segment's chunks, kept by the first pass, in the same order
+                for (int b = 0; b < nexact; b += cap) {
+                    const int m = min(cap, nexact - b);
+                    for (int e = lane; e < m; e += 32) {
+                        const float4* d = wspill + 3 * (size_t)(b + e);
+                        W.q[e] = d[0];
+                        W.c[e] = d[1];
+                        W.pid[e] = __float_as_uint(d[2].x);
+                    }
+                    __syncwarp();
+                    adjoint_flush<NS>(P, W, r, false, m, tS, dtk);
+                }
             } else {
                 auto onfull2 = [&](int m) {
                     adjoint_flush<NS>(P, W, r, false, m, tS, dtk);
@@ -1327,6 +1358,19 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     if (occ < 1) occ = 1;
     const int grid = s->num_sms * occ;
 
+    if (bwd) {
+        // scratch for the chunks of overflowing segments (one region per resident
+        // warp); without it the adjoint re-traverses such segments
+        const size_t need = (size_t)grid * WARPS * SPILL_CAP * 3;
+        if (s->spill_cap < need) {
+            if (s->spill) cudaFree(s->spill);
+            s->spill = nullptr;
+            s->spill_cap = 0;
+            if (cudaMalloc(&s->spill, need * sizeof(float4)) == cudaSuccess) s->spill_cap = need;
+            else { s->spill = nullptr; cudaGetLastError(); }
+        }
+        P.spill = s->spill;
+    }
     void* args[] = {&P};
     RGX_CUDA(s, cudaLaunchKernel(k, dim3(grid), dim3(RGX_BLOCK), args, smem, st));
     return RGX_OK;
