@@ -25,7 +25,8 @@
  *    and returns (and clears) it.  Kernels never trap and never spin without
  *    a bound.
  *  - A scene owns its workspace (BVH, Z-order permutation, packed
- *    parameters, gradient accumulators).  It grows on demand inside
+ *    parameters, gradient accumulators, the adjoint's chunk scratch of
+ *    196 KB per resident warp).  It grows on demand inside
  *    rgx_build_bvh / rgx_render_*; once a scene has seen the largest sizes it
  *    will be used with, later calls allocate nothing and can be captured in a
  *    CUDA graph.

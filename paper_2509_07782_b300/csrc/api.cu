@@ -32,7 +32,7 @@ extern "C" rgx_status rgx_scene_destroy(rgx_scene* s) {
     if (!s) return RGX_OK;
     cudaSetDevice(s->device);
     void* ptrs[] = {s->keys[0], s->keys[1], s->vals[0], s->vals[1], s->hist, s->nodes, s->nodew, s->parent, s->visit,
-                    s->geom, s->shc, s->aux, s->sph, s->perm, s->leafbox, s->bounds, s->root, s->grad, s->cams,
+                    s->geom, s->shc, s->aux, s->perm, s->leafbox, s->bounds, s->root, s->grad, s->cams,
                     s->queue, s->status, s->counters, s->spill};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -177,7 +177,7 @@ __global__ void k_pack(int64_t n, int sh_degree, float sigma_eps, int morton,
                        const float* __restrict__ quats, const float* __restrict__ dens,
                        const float* __restrict__ sh, const uint32_t* __restrict__ sorted_idx,
                        int32_t* __restrict__ perm, float4* __restrict__ geom, float4* __restrict__ shc,
-                       float4* __restrict__ aux, float4* __restrict__ sph, float4* __restrict__ leafbox,
+                       float4* __restrict__ aux, float4* __restrict__ leafbox,
                        unsigned int* __restrict__ status) {
     const int nk = (sh_degree + 1) * (sh_degree + 1);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -218,9 +218,6 @@ __global__ void k_pack(int64_t n, int sh_degree, float sigma_eps, int morton,
         for (int j = 0; j < 12; j++) shc[12 * p + j] = make_float4(c[4 * j], c[4 * j + 1], c[4 * j + 2], c[4 * j + 3]);
         aux[2 * p + 0] = make_float4(qw, qx, qy, qz);
         aux[2 * p + 1] = make_float4(s[0], s[1], s[2], 0.0f);
-        // the ellipsoid's largest semi-axis bounds it by a sphere (padded for rounding)
-        const float smax = fmaxf(fmaxf(s[0], s[1]), s[2]);
-        sph[p] = make_float4(mu[0], mu[1], mu[2], Qe > 0.0f ? sqrtf(Qe) * smax * 1.0001f + 1e-7f : -1.0f);
         // minimal AABB of the Q_eps ellipsoid, padded so float32 rounding never shrinks it
         float4 lo, hi;
         if (Qe > 0.0f) {
@@ -416,7 +413,6 @@ rgx_status rgx_internal_reserve(rgx_scene* s, int64_t n) {
     e = e ? e : grow(&s->geom, 4 * (size_t)c);
     e = e ? e : grow(&s->shc, 12 * (size_t)c);
     e = e ? e : grow(&s->aux, 2 * (size_t)c);
-    e = e ? e : grow(&s->sph, (size_t)c);
     e = e ? e : grow(&s->perm, (size_t)c);
     e = e ? e : grow(&s->leafbox, 2 * (size_t)c);
     size_t hb = (size_t)256 * ((c + RS_TILE - 1) / RS_TILE);
@@ -473,7 +469,7 @@ extern "C" rgx_status rgx_build_bvh(rgx_scene* s, int64_t n, int32_t sh_degree, 
     }
     s->sorted_buf = cur;
     k_pack<<<g, T, 0, st>>>(n, sh_degree, opts->sigma_eps, s->morton, means, scales, quats, densities, sh,
-                            s->vals[cur], s->perm, s->geom, s->shc, s->aux, s->sph, s->leafbox, s->status);
+                            s->vals[cur], s->perm, s->geom, s->shc, s->aux, s->leafbox, s->status);
     if (n == 1) {
         k_single<<<1, 1, 0, st>>>(s->leafbox, s->nodes, s->root);
     } else {

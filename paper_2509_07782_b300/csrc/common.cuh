@@ -8,7 +8,6 @@
 //   geom[4p+3] = (M20, M21, M22, 0)
 //   shc [12p..12p+11] = 48 SH coefficients, (k, channel) channel fastest
 //   aux [2p+0] = raw quaternion (w,x,y,z), aux[2p+1] = (s0, s1, s2, 0)
-//   sph [p]    = (mu, R): a sphere containing the Q_eps ellipsoid (R < 0: empty)
 // so that q(x) = |M (x - mu)|^2 and sigma_l(x) = sigma~ exp(-q/2) (Supp. Sec. 2.1).
 //
 // Internal BVH node i (0 <= i < n-1), 4 x float4 = 64 B, both children's
@@ -55,7 +54,6 @@ struct rgx_scene {
     float4* geom = nullptr;
     float4* shc = nullptr;
     float4* aux = nullptr;
-    float4* sph = nullptr;         // [n] bounding sphere (mu, largest semi-axis) per packed Gaussian
     int32_t* perm = nullptr;       // sorted position -> caller index
     float4* leafbox = nullptr;     // [2n] leaf boxes in sorted order (lo, hi)
     unsigned int* bounds = nullptr;// [8] ordered-int min/max of the means

@@ -49,7 +49,6 @@
 struct MarchParams {
     const float4* __restrict__ geom;
     const float4* __restrict__ shc;
-    const float4* __restrict__ sph;
     const int32_t* __restrict__ perm;
     const float4* __restrict__ nodes;
     const uint4* __restrict__ nodew;
@@ -1326,7 +1325,7 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
                                int32_t* sched_n, cudaStream_t st) {
     MarchParams P;
     memset(&P, 0, sizeof P);
-    P.geom = s->geom; P.shc = s->shc; P.sph = s->sph; P.perm = s->perm; P.nodes = s->nodes; P.nodew = s->nodew; P.root = s->root;
+    P.geom = s->geom; P.shc = s->shc; P.perm = s->perm; P.nodes = s->nodes; P.nodew = s->nodew; P.root = s->root;
     P.n = s->n; P.morton = s->morton;
     P.cams = s->cams; P.ncam = ncam;
     P.flags = o->flags;
