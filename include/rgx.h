@@ -123,10 +123,13 @@ rgx_status rgx_build_bvh(rgx_scene* scene, int64_t n, int32_t sh_degree,
  *   cams       HOST [ncam]  cameras (copied on `stream`)
  *   rgba       [R,4]        output, R = sum_c width_c*height_c, camera-major,
  *                           row-major pixels: (C + T bg, 1 - T)
- *   fwd_state  [R] x rgx_fwd_state_bytes()  per-ray (C, T) kept for the adjoint
- *                           (may be NULL for inference); opaque: the sign bit of
- *                           T records which collection path the ray took, so that
- *                           the adjoint replays it
+ *   fwd_state  [R] x rgx_fwd_state_bytes()  per-ray record kept for the adjoint
+ *                           (may be NULL for inference); opaque: (C, T), the
+ *                           collection path the ray took, and where the scene's
+ *                           tape holds its first chord list.  The tape (scene
+ *                           workspace, hit_cap / 2 entries per ray) keeps the
+ *                           lists of the LAST forward call only; an adjoint given
+ *                           the state of an older call collects them again
  */
 rgx_status rgx_render_forward(rgx_scene* scene, const rgx_camera* cams, int32_t ncam,
                               const rgx_opts* opts, float* rgba, void* fwd_state, void* stream);
@@ -203,7 +206,8 @@ rgx_status rgx_densify_accumulate(int64_t n, const float* means, const float* d_
  * clean) and clear it. */
 rgx_status rgx_sync_status(rgx_scene* scene, void* stream);
 
-/* Bytes of per-ray state written by rgx_render_forward (16: C[3], T). */
+/* Bytes of per-ray state written by rgx_render_forward (32: C[3], T, the collection path, tape offset,
+ * count and tag). */
 size_t rgx_fwd_state_bytes(void);
 
 /* Static description of the last error on this scene (or globally if NULL). */

@@ -33,7 +33,7 @@ extern "C" rgx_status rgx_scene_destroy(rgx_scene* s) {
     cudaSetDevice(s->device);
     void* ptrs[] = {s->keys[0], s->keys[1], s->vals[0], s->vals[1], s->hist, s->nodes, s->nodew, s->parent, s->visit,
                     s->geom, s->shc, s->aux, s->perm, s->leafbox, s->bounds, s->root, s->grad, s->cams,
-                    s->queue, s->status, s->counters, s->spill};
+                    s->queue, s->status, s->counters, s->spill, s->tape};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;
@@ -56,7 +56,7 @@ extern "C" rgx_status rgx_sync_status(rgx_scene* s, void* stream) {
     return (rgx_status)v;
 }
 
-extern "C" size_t rgx_fwd_state_bytes(void) { return 16; }
+extern "C" size_t rgx_fwd_state_bytes(void) { return 32; }
 
 extern "C" const char* rgx_last_error(const rgx_scene* s) { return s ? s->last_error : g_rgx_last_error; }
 

@@ -62,6 +62,9 @@ struct rgx_scene {
     int64_t grad_cap = 0;
     float4* spill = nullptr;       // adjoint scratch: chunk entries of overflowing segments, per resident warp
     size_t spill_cap = 0;          // in float4
+    uint32_t* tape = nullptr;      // packed indices of the last forward's first-window lists
+    size_t tape_cap = 0;           // in entries
+    uint32_t tape_gen = 0, tape_tag = 0;  // tag of the forward call whose lists the tape holds
     // render
     rgx_camera* cams = nullptr; int cams_cap = 0;
     unsigned int* queue = nullptr; // [4] persistent work counters

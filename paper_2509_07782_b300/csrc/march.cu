@@ -45,6 +45,7 @@
 #define SURV 160                                    // leaves awaiting their exact chord (< 32 left + 128 new)
 #define CUT 32                                      // child records of a tile's BVH cut
 #define SPILL_CAP 4096                              // adjoint: chunk entries kept per warp in global scratch
+#define TAPE_CHUNK 2048                             // tape entries a warp reserves at a time
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -67,6 +68,10 @@ struct MarchParams {
     const float4* d_rgba;
     float4* grad;
     float4* spill;  // adjoint: [grid][SPILL_CAP][3] chunk entries (q, c, pid) of an overflowing segment
+    uint32_t* tape;      // packed indices of every taped first-window list (forward writes, adjoint reads)
+    uint32_t* tape_n;    // forward: entries used so far
+    uint32_t tape_cap;   // capacity in entries (0: no tape)
+    uint32_t tape_tag;   // identifies the forward call whose lists the tape holds
     float2* sched;
     int sched_cap;
     int32_t* sched_n;
@@ -656,7 +661,8 @@ __device__ __forceinline__ float far_bound(const float4& lo, const float4& hi, c
 template <int NS, bool BWD>
 __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const rgx_camera& C, int px, int py,
                           const float4& root_lo, const float4& root_hi, const float4& up, const float4& st,
-                          Counters& cnt, bool& whole, float4& o_rgba, float4& o_state, int& o_nrec) {
+                          const uint4& st2, Counters& cnt, bool& whole, uint32_t& tape_base,
+                          uint32_t& tape_left, float4& o_rgba, float4& o_state, uint4& o_tape, int& o_nrec) {
     const int lane = threadIdx.x & 31;
     const int k = lane % NS;
     const int cap = P.hit_cap;
@@ -693,6 +699,8 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
     int nL = 0;
     float w_lo = 1.0f, w_hi = 0.0f;  // current window (empty)
     bool used_whole = false;
+    uint32_t tape_off = 0;
+    int tape_cnt = -1;  // forward: where this ray's first-window list went on the tape (-1: not taped)
     float wlen = 4.0f * (float)NS * (uniform ? P.dt : P.dt_max);
     if (P.n > 0 && tf > tn && skip) {
         // One window over the whole ray [t_n, t_f): when every chord fits in the
@@ -702,7 +710,30 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         // traversal.
         float th = tf;
         bool have = false;
-        if (BWD ? fwd_whole : whole) {
+        // adjoint: the forward's list of this window, from the tape when it is there
+        const bool taped = BWD && fwd_whole && P.tape_cap > 0 && st2.z == P.tape_tag && (int)st2.y >= 0 &&
+                           (int)st2.y <= cap;
+        if (taped) {
+            nL = (int)st2.y;
+            if (lane == 0) cnt.windows++;
+            for (int e = lane; e < nL; e += 32) {
+                const uint32_t q = P.tape[(size_t)st2.x + e];
+                const Chord ch = chord_of(P.geom, q, r);
+                W.q[e] = make_float4(ch.tc, ch.a, ch.qmin, ch.Qe);
+                W.c[e] = make_float4(ch.L, 0.f, 0.f, 0.f);
+                W.tio[e] = make_float2(ch.tin, ch.tout);
+                W.pid[e] = q;
+            }
+            __syncwarp();
+            colour_entries(P, W, 0, nL);
+            have = true;
+            used_whole = true;
+            w_lo = tn;
+            w_hi = tf;
+            float m = INFINITY;
+            for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, tn));
+            th = fminf(warp_min(m), tf);
+        } else if (BWD ? fwd_whole : whole) {
             nL = 0;
             if (lane == 0) cnt.windows++;
             if (w_collect<BWD>(P, W, r, tn, tf, cap, nL, false, NoChunk(), cnt) == 0) {
@@ -713,6 +744,25 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 float m = INFINITY;
                 for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, tn));
                 th = fminf(warp_min(m), tf);
+                if (!BWD && P.tape_cap > 0) {
+                    // tape the list (packed indices in list order) for the adjoint, in the
+                    // warp's current chunk of the tape (a new chunk when it is used up)
+                    if ((uint32_t)nL > tape_left) {
+                        const uint32_t want = max((uint32_t)TAPE_CHUNK, (uint32_t)nL);
+                        uint32_t base = 0;
+                        if (lane == 0) base = atomicAdd(P.tape_n, want);
+                        base = __shfl_sync(FULLMASK, base, 0);
+                        if ((uint64_t)base + want <= (uint64_t)P.tape_cap) { tape_base = base; tape_left = want; }
+                        else tape_left = 0;
+                    }
+                    if ((uint32_t)nL <= tape_left) {
+                        for (int e = lane; e < nL; e += 32) P.tape[(size_t)tape_base + e] = W.pid[e];
+                        tape_off = tape_base;
+                        tape_cnt = nL;
+                        tape_base += (uint32_t)nL;
+                        tape_left -= (uint32_t)nL;
+                    }
+                }
             } else {
                 whole = false;
                 nL = 0;
@@ -945,6 +995,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         o_rgba = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
         // the sign bit of T (>= 0) records the first-window path for the adjoint's replay
         o_state = make_float4(C0, C1, C2, used_whole ? -T : T);
+        o_tape = make_uint4(tape_off, (uint32_t)tape_cnt, P.tape_tag, 0u);
         o_nrec = nrec;
     }
 }
@@ -1129,6 +1180,7 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
     // the scene box (t_f of every ray), in registers for the whole launch
     const float4 root_lo = make_float4(P.root[0], P.root[1], P.root[2], 0.f);
     const float4 root_hi = make_float4(P.root[3], P.root[4], P.root[5], 0.f);
+    uint32_t tape_base = 0, tape_left = 0;  // forward: this warp's current chunk of the tape
     while (true) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(P.queue, 1u);
@@ -1145,10 +1197,12 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
         const bool mine = lane >= l0 && lane < l1;
         Counters cnt = {0, 0, 0, 0, 0, 0, 0};
         float4 my_rgba = make_float4(0.f, 0.f, 0.f, 0.f), my_state = my_rgba;
+        uint4 my_tape = make_uint4(0u, 0xffffffffu, 0u, 0u);
         int my_nrec = 0;
         bool work = P.n > 0;
         // adjoint: lane l holds the upstream gradient and forward state of the tile's ray l
         float4 my_up = make_float4(0.f, 0.f, 0.f, 0.f), my_st = my_up;
+        uint4 my_st2 = make_uint4(0u, 0xffffffffu, 0u, 0u);
         if (BWD && work) {
             // the adjoint skips tiles whose rays all have a zero upstream gradient
             int px, py;
@@ -1156,7 +1210,8 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
             if (mine && tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
                 const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
                 my_up = P.d_rgba[ray];
-                my_st = P.state[ray];
+                my_st = P.state[2 * ray];
+                my_st2 = reinterpret_cast<const uint4*>(P.state)[2 * ray + 1];
                 nz = my_up.x != 0.0f || my_up.y != 0.0f || my_up.z != 0.0f || my_up.w != 0.0f;
             }
             work = __any_sync(FULLMASK, nz);
@@ -1182,24 +1237,31 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
             if (!tile_pixel(cam, lt, l, zt, P.tile_w, P.tile_h, px, py)) continue;
             const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
             float4 o_rgba, o_state;
+            uint4 o_tape = make_uint4(0u, 0xffffffffu, 0u, 0u);
             int o_nrec = 0;
             float4 up_l = make_float4(0.f, 0.f, 0.f, 0.f), st_l = up_l;
+            uint4 st2_l = make_uint4(0u, 0xffffffffu, 0u, 0u);
             if (BWD) {
                 up_l = make_float4(__shfl_sync(FULLMASK, my_up.x, l), __shfl_sync(FULLMASK, my_up.y, l),
                                    __shfl_sync(FULLMASK, my_up.z, l), __shfl_sync(FULLMASK, my_up.w, l));
                 st_l = make_float4(__shfl_sync(FULLMASK, my_st.x, l), __shfl_sync(FULLMASK, my_st.y, l),
                                    __shfl_sync(FULLMASK, my_st.z, l), __shfl_sync(FULLMASK, my_st.w, l));
+                st2_l = make_uint4(__shfl_sync(FULLMASK, my_st2.x, l), __shfl_sync(FULLMASK, my_st2.y, l),
+                                   __shfl_sync(FULLMASK, my_st2.z, l), 0u);
             }
-            march_ray<NS, BWD>(P, W, ray, cam, px, py, root_lo, root_hi, up_l, st_l, cnt, whole, o_rgba, o_state,
-                               o_nrec);
-            if (!BWD && lane == l) { my_rgba = o_rgba; my_state = o_state; my_nrec = o_nrec; }
+            march_ray<NS, BWD>(P, W, ray, cam, px, py, root_lo, root_hi, up_l, st_l, st2_l, cnt, whole, tape_base,
+                               tape_left, o_rgba, o_state, o_tape, o_nrec);
+            if (!BWD && lane == l) { my_rgba = o_rgba; my_state = o_state; my_tape = o_tape; my_nrec = o_nrec; }
         }
         if (!BWD) {
             int px, py;
             if (mine && tile_pixel(cam, lt, lane, zt, P.tile_w, P.tile_h, px, py)) {
                 const int64_t ray = (int64_t)s_pix[c] + (int64_t)py * cam.width + px;
                 P.rgba[ray] = my_rgba;
-                if (P.state) P.state[ray] = my_state;
+                if (P.state) {
+                    P.state[2 * ray] = my_state;
+                    reinterpret_cast<uint4*>(P.state)[2 * ray + 1] = my_tape;
+                }
                 if (P.sched_n) P.sched_n[ray] = my_nrec;
             }
         }
@@ -1340,6 +1402,16 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     P.min_items = 16u * (uint32_t)s->num_sms;
     RGX_CUDA(s, cudaMemcpyAsync(s->cams, cams, sizeof(rgx_camera) * ncam, cudaMemcpyHostToDevice, st));
     RGX_CUDA(s, cudaMemsetAsync(s->queue, 0, sizeof(unsigned), st));
+    // first-window tape: the forward (with a state to hand on) fills it, the adjoint reads it
+    if (!bwd && state && s->tape_cap > 0) {
+        s->tape_gen++;
+        uint32_t tag = (uint32_t)(((uintptr_t)s >> 6) * 0x9E3779B1u) ^ (s->tape_gen * 0x85EBCA77u);
+        s->tape_tag = tag ? tag : 1u;
+        RGX_CUDA(s, cudaMemsetAsync(s->queue + 1, 0, sizeof(unsigned), st));
+        P.tape = s->tape; P.tape_n = s->queue + 1; P.tape_cap = (uint32_t)s->tape_cap; P.tape_tag = s->tape_tag;
+    } else if (bwd && s->tape_cap > 0 && s->tape_tag != 0) {
+        P.tape = s->tape; P.tape_cap = (uint32_t)s->tape_cap; P.tape_tag = s->tape_tag;
+    }
     RGX_CUDA(s, cudaMemsetAsync(s->counters, 0, 8 * sizeof(unsigned long long), st));
     void* k = pick_kernel(o->n_s, bwd);
     const size_t head = ((size_t)(3 * (ncam + 1)) * 4 + 15) & ~(size_t)15;
@@ -1399,6 +1471,19 @@ static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t n
     RGX_CUDA(s, cudaSetDevice(s->device));
     r = ensure_cams(s, ncam);
     if (r) return r;
+    if (state) {
+        // room on the tape for hit_cap / 2 entries per ray on average; a ray that finds no
+        // room is simply not taped (its adjoint collects the window itself)
+        const size_t want = (size_t)R * (size_t)(o->hit_cap / 2);
+        const size_t need = want < (size_t)0x7fffffff ? want : (size_t)0x7fffffff;
+        if (s->tape_cap < need) {
+            if (s->tape) cudaFree(s->tape);
+            s->tape = nullptr;
+            s->tape_cap = 0;
+            if (cudaMalloc(&s->tape, need * sizeof(uint32_t)) == cudaSuccess) s->tape_cap = need;
+            else { s->tape = nullptr; cudaGetLastError(); }
+        }
+    }
     return launch_march(s, cams, ncam, o, false, rgba, state, nullptr, sched, sched_cap, sched_n,
                         (cudaStream_t)stream);
 }

@@ -24,7 +24,7 @@ class CapturedStep:
         self.backward = backward
         dev = self.params[0].device
         self.rgba = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
-        self.state = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
+        self.state = rgx.new_state(cams.n_rays, dev)
         self.d_rgba = d_rgba
         self.grads = [torch.zeros_like(p) for p in self.params]
         self.stream = torch.cuda.Stream(device=dev)

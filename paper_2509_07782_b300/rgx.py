@@ -199,6 +199,11 @@ def rgx_fwd_state_bytes() -> int:
     return int(lib().rgx_fwd_state_bytes())
 
 
+def new_state(n_rays: int, device) -> torch.Tensor:
+    """An uninitialised forward-state buffer: n_rays x rgx_fwd_state_bytes(), as float32 words."""
+    return torch.empty(n_rays, rgx_fwd_state_bytes() // 4, dtype=torch.float32, device=device)
+
+
 def rgx_get_bvh(h, n, stream=None):
     dev = torch.device("cuda", torch.cuda.current_device())
     codes = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
@@ -274,7 +279,7 @@ class Scene:
     def forward(self, cams: Cameras, opts, want_state: bool = True, stream=None, sched_cap: int = 0):
         dev = torch.device("cuda", self.device)
         rgba = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
-        state = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev) if want_state else None
+        state = new_state(cams.n_rays, dev) if want_state else None
         self._keep = cams
         if sched_cap > 0:
             sched = torch.zeros(cams.n_rays, sched_cap, 2, dtype=torch.float32, device=dev)
@@ -301,7 +306,7 @@ class Scene:
         """Pick tile shape / hit_cap (/ N_S) by timing on this scene; returns (RgxOpts, ms)."""
         dev = torch.device("cuda", self.device)
         rgba = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
-        state = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
+        state = new_state(cams.n_rays, dev)
         d_rgba, grads = None, None
         if with_backward:
             d_rgba = torch.randn(cams.n_rays, 4, dtype=torch.float32, device=dev)

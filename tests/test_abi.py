@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_binding_names_match_header(libpath):
     from paper_2509_07782_b300 import rgx
     assert set(rgx.EXPORTS) == set(declared_symbols())
-    assert rgx.rgx_fwd_state_bytes() == 16
+    assert rgx.rgx_fwd_state_bytes() == 32
 
 
 def test_struct_layouts_match_the_c_compiler(libpath, tmp_path):
