@@ -699,6 +699,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
     int nL = 0;
     float w_lo = 1.0f, w_hi = 0.0f;  // current window (empty)
     bool used_whole = false;
+    bool dense = false;  // the last evaluated segment overflowed the list: go straight to chunks
     uint32_t tape_off = 0;
     int tape_cnt = -1;  // forward: where this ray's first-window list went on the tape (-1: not taped)
     float wlen = 4.0f * (float)NS * (uniform ? P.dt : P.dt_max);
@@ -801,7 +802,11 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         bool spill_ok = BWD && P.spill != nullptr;  // adjoint: chunks kept in this warp's scratch
         float4* wspill = BWD && P.spill
             ? P.spill + ((size_t)blockIdx.x * WARPS + (threadIdx.x >> 5)) * SPILL_CAP * 3 : nullptr;
-        if (!(tS >= w_lo && tcut <= w_hi)) {
+        if (!(tS >= w_lo && tcut <= w_hi) && dense) {
+            // dense stretch: a window would overflow again, collect this segment in chunks
+            chunked = true;
+            nL = 0; w_lo = 1.0f; w_hi = 0.0f;
+        } else if (!(tS >= w_lo && tcut <= w_hi)) {
             const float need = te - tS;
             float len = fmaxf(wlen, need);
             while (true) {
@@ -870,6 +875,8 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
             nexact = tot;
             nL = 0;
         }
+        // chunks stay in use while segments keep more than half a list of hits
+        dense = chunked && 2 * nexact > cap;
         if (nexact == 0) {
             if (lane == 0) cnt.skips++;
             if (skip) {
