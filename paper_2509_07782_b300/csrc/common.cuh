@@ -94,23 +94,24 @@ __device__ __forceinline__ float ord2f(unsigned int u) {
 //   1/(2 sqrt(pi)); sqrt(3/(4pi)); sqrt(15/(4pi)), sqrt(5/(16pi)), sqrt(15/(16pi));
 //   sqrt(35/(32pi)), sqrt(105/(4pi)), sqrt(21/(32pi)), sqrt(7/(16pi)), sqrt(105/(16pi)).
 __device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16]) {
-    const float xx = x * x, yy = y * y, zz = z * z;
+    // explicitly rounded: the forward and the adjoint kernel must get the same bits
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
     Y[0] = 0.28209479177387814f;
-    Y[1] = -0.48860251190291992f * y;
-    Y[2] = 0.48860251190291992f * z;
-    Y[3] = -0.48860251190291992f * x;
-    Y[4] = 1.0925484305920792f * x * y;
-    Y[5] = -1.0925484305920792f * y * z;
-    Y[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);
-    Y[7] = -1.0925484305920792f * x * z;
-    Y[8] = 0.54627421529603959f * (xx - yy);
-    Y[9] = -0.59004358992664352f * y * (3.0f * xx - yy);
-    Y[10] = 2.8906114426405538f * x * y * z;
-    Y[11] = -0.45704579946446572f * y * (5.0f * zz - 1.0f);
-    Y[12] = 0.37317633259011540f * z * (5.0f * zz - 3.0f);
-    Y[13] = -0.45704579946446572f * x * (5.0f * zz - 1.0f);
-    Y[14] = 1.4453057213202769f * z * (xx - yy);
-    Y[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+    Y[1] = __fmul_rn(-0.48860251190291992f, y);
+    Y[2] = __fmul_rn(0.48860251190291992f, z);
+    Y[3] = __fmul_rn(-0.48860251190291992f, x);
+    Y[4] = __fmul_rn(__fmul_rn(1.0925484305920792f, x), y);
+    Y[5] = __fmul_rn(__fmul_rn(-1.0925484305920792f, y), z);
+    Y[6] = __fmul_rn(0.31539156525252005f, __fmaf_rn(3.0f, zz, -1.0f));
+    Y[7] = __fmul_rn(__fmul_rn(-1.0925484305920792f, x), z);
+    Y[8] = __fmul_rn(0.54627421529603959f, __fsub_rn(xx, yy));
+    Y[9] = __fmul_rn(__fmul_rn(-0.59004358992664352f, y), __fmaf_rn(3.0f, xx, -yy));
+    Y[10] = __fmul_rn(__fmul_rn(__fmul_rn(2.8906114426405538f, x), y), z);
+    Y[11] = __fmul_rn(__fmul_rn(-0.45704579946446572f, y), __fmaf_rn(5.0f, zz, -1.0f));
+    Y[12] = __fmul_rn(__fmul_rn(0.37317633259011540f, z), __fmaf_rn(5.0f, zz, -3.0f));
+    Y[13] = __fmul_rn(__fmul_rn(-0.45704579946446572f, x), __fmaf_rn(5.0f, zz, -1.0f));
+    Y[14] = __fmul_rn(__fmul_rn(1.4453057213202769f, z), __fsub_rn(xx, yy));
+    Y[15] = __fmul_rn(__fmul_rn(-0.59004358992664352f, x), __fmaf_rn(-3.0f, yy, xx));
 }
 
 // ---------------------------------------------------------------- host helpers

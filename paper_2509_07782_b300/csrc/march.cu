@@ -154,6 +154,11 @@ __device__ __forceinline__ void child_of(uint4 v, float4& lo, float4& hi) {
 }
 
 // Exact chord of the Q_eps ellipsoid of Gaussian p: q(t) = qmin + a (t - tc)^2.
+// a.b in three explicitly rounded steps (a fused multiply-add chain)
+__device__ __forceinline__ float dot3_rn(float a0, float a1, float a2, float b0, float b1, float b2) {
+    return __fmaf_rn(a0, b0, __fmaf_rn(a1, b1, __fmul_rn(a2, b2)));
+}
+
 struct Chord {
     float tc, a, qmin, Qe, L;
     float tin, tout;
@@ -165,26 +170,28 @@ __device__ __forceinline__ Chord chord_of(const float4* __restrict__ geom, int64
     const float4 g1 = __ldg(&geom[4 * p + 1]);
     const float4 g2 = __ldg(&geom[4 * p + 2]);
     const float4 g3 = __ldg(&geom[4 * p + 3]);
+    // every operation rounded explicitly: the adjoint kernel recomputes chords in
+    // other contexts and must get the same bits (no compiler contraction choices)
     Chord c;
-    const float ex = r.ox - g0.x, ey = r.oy - g0.y, ez = r.oz - g0.z;
-    const float y0x = g1.x * ex + g1.y * ey + g1.z * ez;
-    const float y0y = g2.x * ex + g2.y * ey + g2.z * ez;
-    const float y0z = g3.x * ex + g3.y * ey + g3.z * ez;
-    const float ydx = g1.x * r.dx + g1.y * r.dy + g1.z * r.dz;
-    const float ydy = g2.x * r.dx + g2.y * r.dy + g2.z * r.dz;
-    const float ydz = g3.x * r.dx + g3.y * r.dy + g3.z * r.dz;
-    c.a = ydx * ydx + ydy * ydy + ydz * ydz;
-    const float inv_a = 1.0f / c.a;
-    c.tc = -(y0x * ydx + y0y * ydy + y0z * ydz) * inv_a;
-    const float ycx = y0x + c.tc * ydx, ycy = y0y + c.tc * ydy, ycz = y0z + c.tc * ydz;
-    c.qmin = ycx * ycx + ycy * ycy + ycz * ycz;
+    const float ex = __fsub_rn(r.ox, g0.x), ey = __fsub_rn(r.oy, g0.y), ez = __fsub_rn(r.oz, g0.z);
+    const float y0x = dot3_rn(g1.x, g1.y, g1.z, ex, ey, ez);
+    const float y0y = dot3_rn(g2.x, g2.y, g2.z, ex, ey, ez);
+    const float y0z = dot3_rn(g3.x, g3.y, g3.z, ex, ey, ez);
+    const float ydx = dot3_rn(g1.x, g1.y, g1.z, r.dx, r.dy, r.dz);
+    const float ydy = dot3_rn(g2.x, g2.y, g2.z, r.dx, r.dy, r.dz);
+    const float ydz = dot3_rn(g3.x, g3.y, g3.z, r.dx, r.dy, r.dz);
+    c.a = dot3_rn(ydx, ydy, ydz, ydx, ydy, ydz);
+    const float inv_a = __frcp_rn(c.a);
+    c.tc = __fmul_rn(-dot3_rn(y0x, y0y, y0z, ydx, ydy, ydz), inv_a);
+    const float ycx = __fmaf_rn(c.tc, ydx, y0x), ycy = __fmaf_rn(c.tc, ydy, y0y), ycz = __fmaf_rn(c.tc, ydz, y0z);
+    c.qmin = dot3_rn(ycx, ycy, ycz, ycx, ycy, ycz);
     c.Qe = g0.w;
     c.L = g1.w;
-    const float rem = c.Qe - c.qmin;
+    const float rem = __fsub_rn(c.Qe, c.qmin);
     c.ok = (c.Qe > 0.0f) && (rem > 0.0f) && (c.a > 0.0f);
-    const float h = c.ok ? sqrtf(rem * inv_a) : 0.0f;
-    c.tin = c.tc - h;
-    c.tout = c.tc + h;
+    const float h = c.ok ? __fsqrt_rn(__fmul_rn(rem, inv_a)) : 0.0f;
+    c.tin = __fsub_rn(c.tc, h);
+    c.tout = __fadd_rn(c.tc, h);
     return c;
 }
 
@@ -195,13 +202,13 @@ __device__ __forceinline__ void local_frame(const float4* __restrict__ geom, int
     const float4 g1 = __ldg(&geom[4 * p + 1]);
     const float4 g2 = __ldg(&geom[4 * p + 2]);
     const float4 g3 = __ldg(&geom[4 * p + 3]);
-    const float ex = r.ox - g0.x, ey = r.oy - g0.y, ez = r.oz - g0.z;
-    yd[0] = g1.x * r.dx + g1.y * r.dy + g1.z * r.dz;
-    yd[1] = g2.x * r.dx + g2.y * r.dy + g2.z * r.dz;
-    yd[2] = g3.x * r.dx + g3.y * r.dy + g3.z * r.dz;
-    yc[0] = g1.x * ex + g1.y * ey + g1.z * ez + tc * yd[0];
-    yc[1] = g2.x * ex + g2.y * ey + g2.z * ez + tc * yd[1];
-    yc[2] = g3.x * ex + g3.y * ey + g3.z * ez + tc * yd[2];
+    const float ex = __fsub_rn(r.ox, g0.x), ey = __fsub_rn(r.oy, g0.y), ez = __fsub_rn(r.oz, g0.z);
+    yd[0] = dot3_rn(g1.x, g1.y, g1.z, r.dx, r.dy, r.dz);
+    yd[1] = dot3_rn(g2.x, g2.y, g2.z, r.dx, r.dy, r.dz);
+    yd[2] = dot3_rn(g3.x, g3.y, g3.z, r.dx, r.dy, r.dz);
+    yc[0] = __fmaf_rn(tc, yd[0], dot3_rn(g1.x, g1.y, g1.z, ex, ey, ez));
+    yc[1] = __fmaf_rn(tc, yd[1], dot3_rn(g2.x, g2.y, g2.z, ex, ey, ez));
+    yc[2] = __fmaf_rn(tc, yd[2], dot3_rn(g3.x, g3.y, g3.z, ex, ey, ez));
 }
 
 // SH colour c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_k); Y in shared memory.
@@ -214,12 +221,12 @@ __device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_
         // coefficients 12j .. 12j+11 = SH indices 4j .. 4j+3, three channels each
         const float4 v0 = __ldg(&s[3 * j]), v1 = __ldg(&s[3 * j + 1]), v2 = __ldg(&s[3 * j + 2]);
         const float4 y = *reinterpret_cast<const float4*>(Y + 4 * j);
-        r += y.x * v0.x; g += y.x * v0.y; b += y.x * v0.z;
-        r2 += y.y * v0.w; g2 += y.y * v1.x; b2 += y.y * v1.y;
-        r += y.z * v1.z; g += y.z * v1.w; b += y.z * v2.x;
-        r2 += y.w * v2.y; g2 += y.w * v2.z; b2 += y.w * v2.w;
+        r = __fmaf_rn(y.x, v0.x, r); g = __fmaf_rn(y.x, v0.y, g); b = __fmaf_rn(y.x, v0.z, b);
+        r2 = __fmaf_rn(y.y, v0.w, r2); g2 = __fmaf_rn(y.y, v1.x, g2); b2 = __fmaf_rn(y.y, v1.y, b2);
+        r = __fmaf_rn(y.z, v1.z, r); g = __fmaf_rn(y.z, v1.w, g); b = __fmaf_rn(y.z, v2.x, b);
+        r2 = __fmaf_rn(y.w, v2.y, r2); g2 = __fmaf_rn(y.w, v2.z, g2); b2 = __fmaf_rn(y.w, v2.w, b2);
     }
-    c[0] = fmaxf(r + r2, 0.0f); c[1] = fmaxf(g + g2, 0.0f); c[2] = fmaxf(b + b2, 0.0f);
+    c[0] = fmaxf(__fadd_rn(r, r2), 0.0f); c[1] = fmaxf(__fadd_rn(g, g2), 0.0f); c[2] = fmaxf(__fadd_rn(b, b2), 0.0f);
 }
 
 // Minimum over the warp in one reduction: floats mapped to order-preserving
@@ -627,19 +634,19 @@ __device__ __forceinline__ void adjoint_flush(const MarchParams& P, const WS& W,
 // Ray through the centre of pixel (px, py) (pinhole, OpenCV convention); every
 // lane holds the same values.
 __device__ __forceinline__ Ray make_ray(const rgx_camera& C, int px, int py) {
-    Ray r;
-    const float ux = ((float)px + 0.5f - C.cx) / C.fx;
-    const float vy = ((float)py + 0.5f - C.cy) / C.fy;
-    float dx = C.c2w[0] * ux + C.c2w[1] * vy + C.c2w[2];
-    float dy = C.c2w[4] * ux + C.c2w[5] * vy + C.c2w[6];
-    float dz = C.c2w[8] * ux + C.c2w[9] * vy + C.c2w[10];
-    const float inv = 1.0f / sqrtf(dx * dx + dy * dy + dz * dz);
-    r.dx = dx * inv; r.dy = dy * inv; r.dz = dz * inv;
+    Ray r;  // explicitly rounded: both the forward and the adjoint kernel build it
+    const float ux = __fdiv_rn(__fsub_rn(__fadd_rn((float)px, 0.5f), C.cx), C.fx);
+    const float vy = __fdiv_rn(__fsub_rn(__fadd_rn((float)py, 0.5f), C.cy), C.fy);
+    const float dx = __fmaf_rn(C.c2w[0], ux, __fmaf_rn(C.c2w[1], vy, C.c2w[2]));
+    const float dy = __fmaf_rn(C.c2w[4], ux, __fmaf_rn(C.c2w[5], vy, C.c2w[6]));
+    const float dz = __fmaf_rn(C.c2w[8], ux, __fmaf_rn(C.c2w[9], vy, C.c2w[10]));
+    const float inv = __frcp_rn(__fsqrt_rn(dot3_rn(dx, dy, dz, dx, dy, dz)));
+    r.dx = __fmul_rn(dx, inv); r.dy = __fmul_rn(dy, inv); r.dz = __fmul_rn(dz, inv);
     r.ox = C.c2w[3]; r.oy = C.c2w[7]; r.oz = C.c2w[11];
     const float tiny = 1e-20f;
-    r.ix = 1.0f / (fabsf(r.dx) > tiny ? r.dx : copysignf(tiny, r.dx));
-    r.iy = 1.0f / (fabsf(r.dy) > tiny ? r.dy : copysignf(tiny, r.dy));
-    r.iz = 1.0f / (fabsf(r.dz) > tiny ? r.dz : copysignf(tiny, r.dz));
+    r.ix = __frcp_rn(fabsf(r.dx) > tiny ? r.dx : copysignf(tiny, r.dx));
+    r.iy = __frcp_rn(fabsf(r.dy) > tiny ? r.dy : copysignf(tiny, r.dy));
+    r.iz = __frcp_rn(fabsf(r.dz) > tiny ? r.dz : copysignf(tiny, r.dz));
     return r;
 }
 
@@ -1044,26 +1051,30 @@ struct Frustum {
 };
 
 __device__ __forceinline__ float3 cam_dir(const rgx_camera& C, float u, float v) {
-    return make_float3(C.c2w[0] * u + C.c2w[1] * v + C.c2w[2], C.c2w[4] * u + C.c2w[5] * v + C.c2w[6],
-                       C.c2w[8] * u + C.c2w[9] * v + C.c2w[10]);
+    return make_float3(__fmaf_rn(C.c2w[0], u, __fmaf_rn(C.c2w[1], v, C.c2w[2])),
+                       __fmaf_rn(C.c2w[4], u, __fmaf_rn(C.c2w[5], v, C.c2w[6])),
+                       __fmaf_rn(C.c2w[8], u, __fmaf_rn(C.c2w[9], v, C.c2w[10])));
 }
 
 __device__ Frustum tile_frustum(const rgx_camera& C, int pxa, int pya, int pxb, int pyb) {
-    const float u0 = ((float)pxa - C.cx) / C.fx, u1 = ((float)pxb + 1.0f - C.cx) / C.fx;
-    const float v0 = ((float)pya - C.cy) / C.fy, v1 = ((float)pyb + 1.0f - C.cy) / C.fy;
+    // explicitly rounded: both the forward and the adjoint kernel build the tile's cut from it
+    const float u0 = __fdiv_rn(__fsub_rn((float)pxa, C.cx), C.fx);
+    const float u1 = __fdiv_rn(__fsub_rn(__fadd_rn((float)pxb, 1.0f), C.cx), C.fx);
+    const float v0 = __fdiv_rn(__fsub_rn((float)pya, C.cy), C.fy);
+    const float v1 = __fdiv_rn(__fsub_rn(__fadd_rn((float)pyb, 1.0f), C.cy), C.fy);
     const float3 d00 = cam_dir(C, u0, v0), d10 = cam_dir(C, u1, v0), d01 = cam_dir(C, u0, v1),
                  d11 = cam_dir(C, u1, v1);
-    const float3 dc = cam_dir(C, 0.5f * (u0 + u1), 0.5f * (v0 + v1));
+    const float3 dc = cam_dir(C, __fmul_rn(0.5f, __fadd_rn(u0, u1)), __fmul_rn(0.5f, __fadd_rn(v0, v1)));
     const float ox = C.c2w[3], oy = C.c2w[7], oz = C.c2w[11];
     const float3 ea[4] = {d00, d10, d00, d01}, eb[4] = {d01, d11, d10, d11};
     Frustum F;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        float nx = ea[i].y * eb[i].z - ea[i].z * eb[i].y;
-        float ny = ea[i].z * eb[i].x - ea[i].x * eb[i].z;
-        float nz = ea[i].x * eb[i].y - ea[i].y * eb[i].x;
-        if (nx * dc.x + ny * dc.y + nz * dc.z < 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
-        F.pl[i] = make_float4(nx, ny, nz, -(nx * ox + ny * oy + nz * oz));
+        float nx = __fmaf_rn(ea[i].y, eb[i].z, -__fmul_rn(ea[i].z, eb[i].y));
+        float ny = __fmaf_rn(ea[i].z, eb[i].x, -__fmul_rn(ea[i].x, eb[i].z));
+        float nz = __fmaf_rn(ea[i].x, eb[i].y, -__fmul_rn(ea[i].y, eb[i].x));
+        if (dot3_rn(nx, ny, nz, dc.x, dc.y, dc.z) < 0.0f) { nx = -nx; ny = -ny; nz = -nz; }
+        F.pl[i] = make_float4(nx, ny, nz, -dot3_rn(nx, ny, nz, ox, oy, oz));
     }
     return F;
 }
@@ -1075,8 +1086,9 @@ __device__ __forceinline__ bool box_outside(const Frustum& F, float4 lo, float4 
     for (int i = 0; i < 4; i++) {
         const float4 p = F.pl[i];
         const float x = p.x > 0.0f ? hi.x : lo.x, y = p.y > 0.0f ? hi.y : lo.y, z = p.z > 0.0f ? hi.z : lo.z;
-        const float v = p.x * x + p.y * y + p.z * z + p.w;
-        const float mag = fabsf(p.x * x) + fabsf(p.y * y) + fabsf(p.z * z) + fabsf(p.w);
+        const float v = __fadd_rn(dot3_rn(p.x, p.y, p.z, x, y, z), p.w);
+        const float mag = __fadd_rn(__fadd_rn(fabsf(__fmul_rn(p.x, x)), fabsf(__fmul_rn(p.y, y))),
+                                    __fadd_rn(fabsf(__fmul_rn(p.z, z)), fabsf(p.w)));
         if (v < -1e-5f * mag) return true;
     }
     return false;
