@@ -13,6 +13,8 @@
 //   k_karras    binary radix tree over the sorted codes (Karras 2012), one thread
 //               per internal node, ties broken by sorted position
 //   k_refit     bottom-up AABB union with per-node arrival counters
+//   k_widen     4-wide traversal records: per internal node its (up to) four
+//               grandchildren as half-precision boxes, rounded outward
 #include <stdio.h>
 #include <cuda_fp16.h>
 #include "common.cuh"
