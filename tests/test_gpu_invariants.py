@@ -126,3 +126,32 @@ def test_bad_parameters_and_segment_limit_reported():
     r2 = gpu_render(sc, w.cameras, opts_with(w.options, max_segments=2))
     assert r2["status"] & rgx.RGX_ERR_ITER_LIMIT
     torch.cuda.synchronize()
+
+
+def test_adjoint_with_a_stale_state_collects_again_and_matches():
+    # The scene's tape keeps the first chord lists of the LAST forward call only.
+    # An adjoint given the state of an older call must notice (tag mismatch),
+    # collect the lists again by traversal and replay the same march (no replay
+    # error); gradients then agree up to the order of the float atomics.
+    w = synth.workload("torus_100k", n=30000, scale_res=0.25)
+    sc = rgx.Scene()
+    t = rgx.scene_tensors(w.scene)
+    o = rgx.make_opts(w.options)
+    sc.build(*t, o)
+    cb = rgx.Cameras(w.cameras)
+    d = torch.as_tensor(np.random.default_rng(5).normal(size=(cb.n_rays, 4)), dtype=torch.float32, device="cuda")
+
+    def adjoint(state):
+        g = [torch.zeros_like(x) for x in t]
+        sc.backward(cb, o, state, d, g)
+        assert sc.status() == 0  # no RGX_ERR_REPLAY
+        return [x.cpu().numpy() for x in g], sc.counters()["node_visits"]
+
+    rgba1, st1 = sc.forward(cb, o)
+    taped, visits_taped = adjoint(st1)
+    other = rgx.Cameras([synth.rescale_camera(w.cameras[0], 0.5)])
+    sc.forward(other, o)  # overwrites the tape
+    again, visits_again = adjoint(st1)
+    assert visits_again > 2 * visits_taped  # the lists were collected again
+    for a, b in zip(taped, again):
+        np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * np.abs(a).max())
