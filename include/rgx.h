@@ -107,8 +107,8 @@ rgx_status rgx_scene_destroy(rgx_scene* scene);
  *
  * Steps (all on `stream`): scene bounds of the means, 30/63-bit Morton codes,
  * LSD radix sort of (code, index), Karras radix tree, bottom-up AABB refit,
- * and packing of the parameters into float4 records (in Z-order with
- * RGX_MORTON, else in caller order).  The arrays are read during this call
+ * 4-wide half-precision traversal records, and packing of the parameters into
+ * float4 records (in Z-order with RGX_MORTON, else in caller order).  The arrays are read during this call
  * only; the scene keeps its own packed copy.  n may be 0.
  */
 rgx_status rgx_build_bvh(rgx_scene* scene, int64_t n, int32_t sh_degree,
@@ -153,7 +153,12 @@ rgx_status rgx_render_forward_sched(rgx_scene* scene, const rgx_camera* cams, in
  * boundary, the schedule and termination are held fixed (piecewise
  * constant).  Rays whose d_rgba row is zero contribute nothing and are
  * skipped.  Must follow rgx_render_forward with the same cameras and options
- * on a scene not rebuilt in between.
+ * on a scene not rebuilt in between, and be given the fwd_state that forward
+ * wrote.  With the state of the scene's last forward call the first chord
+ * lists come from the tape; with an older state they are collected again
+ * (same result, more work).  Segments whose chords overflow hit_cap are kept
+ * in the scene's per-warp scratch between the two adjoint passes; if that
+ * scratch cannot be allocated they are traversed twice instead.
  */
 rgx_status rgx_render_backward(rgx_scene* scene, const rgx_camera* cams, int32_t ncam,
                                const rgx_opts* opts, const void* fwd_state, const float* d_rgba,
