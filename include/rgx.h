@@ -127,7 +127,7 @@ rgx_status rgx_build_bvh(rgx_scene* scene, int64_t n, int32_t sh_degree,
  *                           (may be NULL for inference); opaque: (C, T), the
  *                           collection path the ray took, and where the scene's
  *                           tape holds its first chord list.  The tape (scene
- *                           workspace, hit_cap / 2 entries per ray) keeps the
+ *                           workspace, hit_cap / 6 entries of 48 B per ray) keeps the
  *                           lists of the LAST forward call only; an adjoint given
  *                           the state of an older call collects them again
  */

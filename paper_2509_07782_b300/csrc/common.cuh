@@ -62,7 +62,7 @@ struct rgx_scene {
     int64_t grad_cap = 0;
     float4* spill = nullptr;       // adjoint scratch: chunk entries of overflowing segments, per resident warp
     size_t spill_cap = 0;          // in float4
-    uint32_t* tape = nullptr;      // packed indices of the last forward's first-window lists
+    float4* tape = nullptr;        // the last forward's first-window lists: 3 planes of tape_cap float4
     size_t tape_cap = 0;           // in entries
     uint32_t tape_gen = 0, tape_tag = 0;  // tag of the forward call whose lists the tape holds
     // render

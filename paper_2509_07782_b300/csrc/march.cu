@@ -68,7 +68,8 @@ struct MarchParams {
     const float4* d_rgba;
     float4* grad;
     float4* spill;  // adjoint: [grid][SPILL_CAP][3] chunk entries (q, c, pid) of an overflowing segment
-    uint32_t* tape;      // packed indices of every taped first-window list (forward writes, adjoint reads)
+    float4* tape;        // taped first-window lists, three planes of tape_cap entries: (t_c, a, q_min, Q_eps),
+                         // (log2 sigma~, colour), (t_in, t_out, packed index bits, 0); forward writes, adjoint reads
     uint32_t* tape_n;    // forward: entries used so far
     uint32_t tape_cap;   // capacity in entries (0: no tape)
     uint32_t tape_tag;   // identifies the forward call whose lists the tape holds
@@ -724,16 +725,17 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         if (taped) {
             nL = (int)st2.y;
             if (lane == 0) cnt.windows++;
+            const float4* tq = P.tape + st2.x;
+            const float4* tc = tq + P.tape_cap;
+            const float4* tx = tc + P.tape_cap;
             for (int e = lane; e < nL; e += 32) {
-                const uint32_t q = P.tape[(size_t)st2.x + e];
-                const Chord ch = chord_of(P.geom, q, r);
-                W.q[e] = make_float4(ch.tc, ch.a, ch.qmin, ch.Qe);
-                W.c[e] = make_float4(ch.L, 0.f, 0.f, 0.f);
-                W.tio[e] = make_float2(ch.tin, ch.tout);
-                W.pid[e] = q;
+                const float4 x = tx[e];
+                W.q[e] = tq[e];
+                W.c[e] = tc[e];
+                W.tio[e] = make_float2(x.x, x.y);
+                W.pid[e] = __float_as_uint(x.z);
             }
             __syncwarp();
-            colour_entries(P, W, 0, nL);
             have = true;
             used_whole = true;
             w_lo = tn;
@@ -753,7 +755,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, tn));
                 th = fminf(warp_min(m), tf);
                 if (!BWD && P.tape_cap > 0) {
-                    // tape the list (packed indices in list order) for the adjoint, in the
+                    // tape the finished list (entries in list order) for the adjoint, in the
                     // warp's current chunk of the tape (a new chunk when it is used up)
                     if ((uint32_t)nL > tape_left) {
                         const uint32_t want = max((uint32_t)TAPE_CHUNK, (uint32_t)nL);
@@ -764,7 +766,15 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                         else tape_left = 0;
                     }
                     if ((uint32_t)nL <= tape_left) {
-                        for (int e = lane; e < nL; e += 32) P.tape[(size_t)tape_base + e] = W.pid[e];
+                        float4* tq = P.tape + tape_base;
+                        float4* tc = tq + P.tape_cap;
+                        float4* tx = tc + P.tape_cap;
+                        for (int e = lane; e < nL; e += 32) {
+                            const float2 io = W.tio[e];
+                            tq[e] = W.q[e];
+                            tc[e] = W.c[e];
+                            tx[e] = make_float4(io.x, io.y, __uint_as_float(W.pid[e]), 0.f);
+                        }
                         tape_off = tape_base;
                         tape_cnt = nL;
                         tape_base += (uint32_t)nL;
@@ -1491,15 +1501,15 @@ static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t n
     r = ensure_cams(s, ncam);
     if (r) return r;
     if (state) {
-        // room on the tape for hit_cap / 2 entries per ray on average; a ray that finds no
-        // room is simply not taped (its adjoint collects the window itself)
-        const size_t want = (size_t)R * (size_t)(o->hit_cap / 2);
+        // room on the tape for hit_cap / 6 entries of 48 B per ray on average; a ray that
+        // finds no room is simply not taped (its adjoint collects the window itself)
+        const size_t want = (size_t)R * (size_t)(o->hit_cap / 6);
         const size_t need = want < (size_t)0x7fffffff ? want : (size_t)0x7fffffff;
         if (s->tape_cap < need) {
             if (s->tape) cudaFree(s->tape);
             s->tape = nullptr;
             s->tape_cap = 0;
-            if (cudaMalloc(&s->tape, need * sizeof(uint32_t)) == cudaSuccess) s->tape_cap = need;
+            if (cudaMalloc(&s->tape, 3 * need * sizeof(float4)) == cudaSuccess) s->tape_cap = need;
             else { s->tape = nullptr; cudaGetLastError(); }
         }
     }
