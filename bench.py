@@ -162,19 +162,21 @@ def alu_model(evals, hits, segs, rays, ns, backward: bool):
 
     Per (sample, Gaussian) evaluation: sample offset (FMA), quadratic form
     (MUL + FMA), exponent (FMA), 1 ex2 on the SFU, density add, 3 colour FMA
-    -> 14 FP32 FLOPs + 1 ex2; the adjoint replays that and adds the
-    dL/dg product (3 FMA + mul), 3 moment FMA (+2 mul) and 3 colour-gradient FMA
-    -> +22 FLOPs.  Per (ray, segment, Gaussian) hit: chord solve (~60 FLOPs),
-    SH colour (48 FMA = 96 FLOPs); the adjoint doubles these and adds the
-    moment expansion (~60) and 59 atomically added floats.  One ex2 is
-    counted as 16 FLOP-equivalents (128 FP32 lanes x 2 vs 16 SFU results per
-    SM per clock), so the FP32 pipe peak is the single denominator.
+    -> 14 FP32 FLOPs + 1 ex2; the adjoint evaluates twice (the replayed sums,
+    then its own sample loop) and adds the dL/dg product (3 FMA + mul), 3
+    moment FMA (+2 mul) and 3 colour-gradient FMA -> 2 x 30 + 22.  Per (ray,
+    segment, Gaussian) hit: chord solve (~60 FLOPs) and SH colour (48 FMA = 96
+    FLOPs) in the forward; in the adjoint, whose lists come from the forward's
+    tape, the local frame and moment expansion (~60) and the SH gradient
+    (48 MUL x 2 = 96), added with 15 float4 atomics.  One ex2 is counted as
+    16 FLOP-equivalents (128 FP32 lanes x 2 vs 16 SFU results per SM per
+    clock), so the FP32 pipe peak is the single denominator.
     """
     per_eval = 14 + 16
     per_hit = 60 + 96
     if backward:
         per_eval = 2 * per_eval + 22
-        per_hit = 2 * per_hit + 60
+        per_hit = 60 + 96
     return evals * per_eval + hits * per_hit
 
 
