@@ -153,8 +153,34 @@ def launches_per_step(opts) -> int:
     return build + 1 + 2                  # forward march; backward march + finalize
 
 
-def algorithmic_counts(counters_fwd, counters_bwd):
-    return counters_fwd, counters_bwd
+def touched_gaussians(grads) -> int:
+    """Gaussians with a non-zero entry in any of the five gradient tensors of a
+    dense random upstream gradient: the Gaussians the march had to read (a lower
+    bound, since a Gaussian whose every sample falls outside its truncation
+    contributes nothing)."""
+    import torch
+    n = grads[0].shape[0]
+    return int(torch.cat([g.reshape(n, -1) for g in grads], 1).ne(0).any(1).sum())
+
+
+def hbm_roofline(n_touched: int, rays: int, seconds: float, backward: bool, peak_gbs: float, traffic=None):
+    """Algorithmic HBM bytes of one march launch and the bandwidth they imply.
+
+    Forward: each touched Gaussian's 236-byte parameter record and one 32-byte
+    BVH node per touched Gaussian read once, 16 B RGBA + 16 B state per ray
+    written.  Adjoint: the same reads, 16 B dL/dRGBA + 16 B state per ray, and
+    each touched Gaussian's 236 bytes of gradient read and written once.  Beside
+    them the measured DRAM bytes of the same kernel (ncu), when known.
+    """
+    per_g = 236 + 32 + (2 * 236 if backward else 0)
+    alg = n_touched * per_g + rays * 32
+    out = {"algorithmic_bytes": alg, "achieved": alg / seconds / 1e9, "peak": peak_gbs, "unit": "GB/s",
+           "frac": alg / seconds / 1e9 / peak_gbs, "touched_gaussians": n_touched}
+    if traffic is not None:
+        out["dram_bytes"] = traffic
+        out["dram_gbs"] = traffic / seconds / 1e9
+        out["dram_frac"] = traffic / seconds / 1e9 / peak_gbs
+    return out
 
 
 def alu_model(evals, hits, segs, rays, ns, backward: bool):
@@ -300,6 +326,7 @@ def run_rgx(args, rank, world, local):
     sc.backward(cams, opts, state, upstream, grads)
     cb = sc.counters()
     torch.cuda.synchronize()
+    n_touched = touched_gaussians(grads)
 
     # e2e through the C-ABI with host buffers: H2D params + upstream, D2H grads + rgba
     host_in = [x.cpu().pin_memory() for x in t] + [upstream.cpu().pin_memory()]
@@ -371,7 +398,7 @@ def run_rgx(args, rank, world, local):
                 e2e=dict(value=whole_job_mrays(world, R, 1, e2e_ms), unit="Mrays/s", h2d_bytes_per_step=h2d,
                          d2h_bytes_per_step=d2h, ms_per_step=e2e_ms),
                 counters_fwd=cf, counters_bwd=cb, clocks=clocks, status=st, plain=plain, opts=w.options, tuned=tuned,
-                n=w.scene.n, steps_launches=launches_per_step(w.options) * args.steps)
+                n=w.scene.n, n_touched=n_touched, steps_launches=launches_per_step(w.options) * args.steps)
 
 
 def _oracle_rate(w, cam, P, threads: int, max_seconds: float, npix_start: int):
@@ -586,6 +613,10 @@ def main():
                 "traffic": profiled_traffic(kname),
                 "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived), HBM {src} "
                                f"{peaks.get('hbm_gbs')} GB/s"}
+    hbm = hbm_roofline(r["n_touched"], r["R"], bwd_s if dominant_is_bwd else fwd_s, dominant_is_bwd,
+                       float(peaks.get("hbm_gbs", 6400.0)), roofline["traffic"])
+    hbm["kernel"] = kname
+    hbm["peak_source"] = f"{src} copy bandwidth"
     out = {
         "metric": METRIC, "value": r["value"], "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -602,6 +633,7 @@ def main():
                              "fwd_bwd": ((r["plain"]["fwd_ms"] + r["plain"]["bwd_ms"]) / (r["fwd_ms"] + r["bwd_ms"]))
                              if r["plain"] else None},
         "roofline": roofline,
+        "hbm_roofline": hbm,
         "work": {"fwd": cf, "bwd": cb},
         "e2e": r["e2e"], "gpu_launches": r["steps_launches"], "clocks": r["clocks"],
         "device_status": r["status"],

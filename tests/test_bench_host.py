@@ -1,0 +1,41 @@
+"""Host-side arithmetic of bench.py that needs no GPU: the count of Gaussians a
+march touched (from its gradients) and the algorithmic-HBM roofline built on it."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import bench
+
+
+def _grads(n, nk=16):
+    return [torch.zeros(n, 3), torch.zeros(n, 3), torch.zeros(n, 4), torch.zeros(n), torch.zeros(n, nk, 3)]
+
+
+def test_touched_counts_gaussians_with_any_nonzero_gradient_entry():
+    g = _grads(7)
+    assert bench.touched_gaussians(g) == 0
+    g[3][2] = 1.0          # density only
+    g[4][5, 15, 2] = -3.0  # last SH coefficient of the last channel only
+    g[0][5, 0] = 2.0       # same Gaussian again: counted once
+    g[2][6, 3] = 1e-30     # tiny but non-zero
+    assert bench.touched_gaussians(g) == 3
+
+
+def test_touched_count_does_not_broadcast_between_tensor_shapes():
+    # a (N,) tensor beside (N,3) ones must not form an N x N mask
+    n = 1000
+    g = _grads(n)
+    g[3][:] = 1.0
+    assert bench.touched_gaussians(g) == n
+
+
+def test_hbm_roofline_counts_the_method_bytes():
+    f = bench.hbm_roofline(1000, 64, 1e-3, False, 6505.6)
+    assert f["algorithmic_bytes"] == 1000 * (236 + 32) + 64 * 32
+    b = bench.hbm_roofline(1000, 64, 1e-3, True, 6505.6, traffic=10_000_000)
+    assert b["algorithmic_bytes"] == 1000 * (236 + 32 + 2 * 236) + 64 * 32
+    assert np.isclose(b["achieved"], b["algorithmic_bytes"] / 1e-3 / 1e9)
+    assert np.isclose(b["frac"], b["achieved"] / 6505.6)
+    assert np.isclose(b["dram_gbs"], 10.0) and np.isclose(b["dram_frac"], 10.0 / 6505.6)
+    assert "dram_bytes" not in f
