@@ -131,19 +131,20 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------------------------
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summaries, or None when there is none for that pair or the kernel source
+    changed since the counters were taken."""
     import glob
     import hashlib
     src = os.path.join(ROOT, "paper_2509_07782_b300", "csrc", "march.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             parts = line.split()
-            if len(parts) == 5 and parts[0] == "traffic_bytes_per_launch" and parts[1] == kernel:
-                if parts[4] == sha:
-                    return int(parts[2])
+            if len(parts) == 6 and parts[0] == "traffic_bytes_per_launch" and parts[1] == workload \
+                    and parts[2] == kernel and parts[4] == "src_sha256" and parts[5] == sha:
+                return int(parts[3])
     return None
 
 
@@ -610,7 +611,7 @@ def main():
     kname = "k_march<16,1>" if dominant_is_bwd else "k_march<16,0>"
     roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": profiled_traffic(kname),
+                "traffic": profiled_traffic(kname, args.workload),
                 "peak_source": f"148 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (derived), HBM {src} "
                                f"{peaks.get('hbm_gbs')} GB/s"}
     hbm = hbm_roofline(r["n_touched"], r["R"], bwd_s if dominant_is_bwd else fwd_s, dominant_is_bwd,

@@ -39,3 +39,22 @@ def test_hbm_roofline_counts_the_method_bytes():
     assert np.isclose(b["frac"], b["achieved"] / 6505.6)
     assert np.isclose(b["dram_gbs"], 10.0) and np.isclose(b["dram_frac"], 10.0 / 6505.6)
     assert "dram_bytes" not in f
+
+
+def test_profiled_traffic_is_keyed_on_workload_kernel_and_source_hash(monkeypatch, tmp_path):
+    import hashlib
+    src = tmp_path / "paper_2509_07782_b300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "march.cu").write_text("// kernel v1\n")
+    sha = hashlib.sha256(b"// kernel v1\n").hexdigest()[:16]
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "a.md").write_text(
+        f"traffic_bytes_per_launch torus_100k k_march<16,1> 123 src_sha256 {sha}\n"
+        f"traffic_bytes_per_launch outdoor_3m k_march<16,1> 456 src_sha256 {sha}\n"
+        "traffic_bytes_per_launch outdoor_3m k_march<16,0> 789 src_sha256 0000000000000000\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("k_march<16,1>", "torus_100k") == 123
+    assert bench.profiled_traffic("k_march<16,1>", "outdoor_3m") == 456
+    assert bench.profiled_traffic("k_march<16,1>", "plain_2k") is None
+    # counters taken on another source version do not count
+    assert bench.profiled_traffic("k_march<16,0>", "outdoor_3m") is None
