@@ -12,8 +12,12 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - Array arguments are DEVICE pointers owned by the caller: contiguous,
- *    float32 unless stated, on the scene's device.  Camera arrays are HOST
- *    pointers (pinned memory is best: they are copied with cudaMemcpyAsync).
+ *    float32 unless stated, on the scene's device, and at least as long as
+ *    stated (a plain pointer cannot be checked here: a host pointer or a
+ *    short buffer is an out-of-bounds access on the device).  Camera arrays
+ *    are HOST pointers, copied with a stream-ordered cudaMemcpyAsync: a
+ *    pinned array is read when the stream reaches the copy, so it must stay
+ *    alive and unchanged until then (a pageable one is staged during the call).
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
  *    default stream.  Every call only enqueues work on it and returns; no
  *    call synchronises except rgx_sync_status.

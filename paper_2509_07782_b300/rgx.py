@@ -7,7 +7,12 @@ raises -- there is no CPU or PyTorch fallback.
 Module-level functions carry the C names (``rgx_build_bvh``,
 ``rgx_render_forward``, ``rgx_render_backward`` ...) and take torch CUDA
 tensors; ``Scene`` and ``Cameras`` are small owners of the opaque handle and
-of the pinned camera array.
+of the pinned camera array.  Before each call the binding checks what a plain
+pointer cannot carry -- every tensor on the GPU, contiguous, of the element
+type the header states and at least as long as the call reads or writes --
+and raises ValueError instead of passing a bad address to a kernel.  A
+``Cameras`` object must outlive the work enqueued with it: its pinned array is
+read when the stream reaches the copy (``Scene`` keeps the last one alive).
 """
 from __future__ import annotations
 
@@ -106,12 +111,32 @@ def _check(code, handle=None):
         raise RgxError(code, msg)
 
 
-def _ptr(t):
+def _ptr(t, name: str = "tensor", numel: int | None = None, dtype=torch.float32, nbytes: int | None = None,
+         optional: bool = True):
+    """Device pointer of a tensor after the checks the C side cannot make on a
+    plain pointer: a contiguous CUDA tensor of the expected dtype holding at
+    least `numel` elements (or `nbytes` bytes, for opaque buffers)."""
     if t is None:
-        return None
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
-        raise ValueError("tensor must be contiguous")
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    if nbytes is not None and t.numel() * t.element_size() < nbytes:
+        raise ValueError(f"{name} holds {t.numel() * t.element_size()} bytes, needs {nbytes}")
     return C.c_void_p(t.data_ptr())
+
+
+def _same_device(*ts):
+    devs = {t.device for t in ts if isinstance(t, torch.Tensor)}
+    if len(devs) > 1:
+        raise ValueError(f"tensors on different devices: {sorted(map(str, devs))}")
 
 
 def _stream(stream=None):
@@ -168,27 +193,63 @@ def rgx_scene_destroy(h):
     lib().rgx_scene_destroy(h)
 
 
+def _param_ptrs(n, sh_degree, means, scales, quats, densities, sh, prefix=""):
+    """Pointers of the five per-Gaussian arrays (parameters or their gradients)."""
+    if not 0 <= int(sh_degree) <= 3:
+        raise ValueError("sh_degree must be in 0..3")
+    nk = (int(sh_degree) + 1) ** 2
+    req = n > 0
+    _same_device(means, scales, quats, densities, sh)
+    return (_ptr(means, prefix + "means", 3 * n, optional=not req),
+            _ptr(scales, prefix + "scales", 3 * n, optional=not req),
+            _ptr(quats, prefix + "quats", 4 * n, optional=not req),
+            _ptr(densities, prefix + "densities", n, optional=not req),
+            _ptr(sh, prefix + "sh", nk * 3 * n, optional=not req))
+
+
 def rgx_build_bvh(h, means, scales, quats, densities, sh, sh_degree, opts, stream=None):
     n = int(means.shape[0])
-    _check(lib().rgx_build_bvh(h, n, int(sh_degree), _ptr(means), _ptr(scales), _ptr(quats), _ptr(densities),
-                               _ptr(sh), C.byref(opts), _stream(stream)), h)
+    ptrs = _param_ptrs(n, sh_degree, means, scales, quats, densities, sh)
+    _check(lib().rgx_build_bvh(h, n, int(sh_degree), *ptrs, C.byref(opts), _stream(stream)), h)
+
+
+def _state_bytes(cams: Cameras) -> int:
+    return cams.n_rays * rgx_fwd_state_bytes()
 
 
 def rgx_render_forward(h, cams: Cameras, opts, rgba, state=None, stream=None):
-    _check(lib().rgx_render_forward(h, cams.ptr, cams.count, C.byref(opts), _ptr(rgba), _ptr(state),
-                                    _stream(stream)), h)
+    R = cams.n_rays
+    _same_device(rgba, state)
+    p_rgba = _ptr(rgba, "rgba", 4 * R, optional=False)
+    p_state = _ptr(state, "fwd_state", dtype=None, nbytes=_state_bytes(cams))
+    _check(lib().rgx_render_forward(h, cams.ptr, cams.count, C.byref(opts), p_rgba, p_state, _stream(stream)), h)
 
 
 def rgx_render_forward_sched(h, cams: Cameras, opts, rgba, state, sched, sched_n, stream=None):
-    _check(lib().rgx_render_forward_sched(h, cams.ptr, cams.count, C.byref(opts), _ptr(rgba), _ptr(state),
-                                          _ptr(sched), int(sched.shape[1]), _ptr(sched_n), _stream(stream)), h)
+    R = cams.n_rays
+    if sched is None or sched.dim() != 3 or sched.shape[2] != 2:
+        raise ValueError("sched must be a [R, sched_cap, 2] tensor")
+    cap = int(sched.shape[1])
+    _same_device(rgba, state, sched, sched_n)
+    p_rgba = _ptr(rgba, "rgba", 4 * R, optional=False)
+    p_state = _ptr(state, "fwd_state", dtype=None, nbytes=_state_bytes(cams))
+    p_sched = _ptr(sched, "sched", 2 * cap * R, optional=False)
+    p_n = _ptr(sched_n, "sched_n", R, dtype=torch.int32, optional=False)
+    _check(lib().rgx_render_forward_sched(h, cams.ptr, cams.count, C.byref(opts), p_rgba, p_state, p_sched, cap,
+                                          p_n, _stream(stream)), h)
 
 
 def rgx_render_backward(h, cams: Cameras, opts, state, d_rgba, d_means, d_scales, d_quats, d_densities, d_sh,
-                        stream=None):
-    _check(lib().rgx_render_backward(h, cams.ptr, cams.count, C.byref(opts), _ptr(state), _ptr(d_rgba),
-                                     _ptr(d_means), _ptr(d_scales), _ptr(d_quats), _ptr(d_densities), _ptr(d_sh),
-                                     _stream(stream)), h)
+                        stream=None, n=None, sh_degree: int = 3):
+    """`n` (the scene's Gaussian count, when known) and `sh_degree` size-check the
+    gradient arrays; without `n` only their dtype and placement are checked."""
+    R = cams.n_rays
+    _same_device(state, d_rgba, d_means, d_scales, d_quats, d_densities, d_sh)
+    p_state = _ptr(state, "fwd_state", dtype=None, nbytes=_state_bytes(cams), optional=False)
+    p_d = _ptr(d_rgba, "d_rgba", 4 * R, optional=False)
+    g = _param_ptrs(int(n) if n is not None else 0, sh_degree, d_means, d_scales, d_quats, d_densities, d_sh,
+                    prefix="d_")
+    _check(lib().rgx_render_backward(h, cams.ptr, cams.count, C.byref(opts), p_state, p_d, *g, _stream(stream)), h)
 
 
 def rgx_sync_status(h, stream=None) -> int:
@@ -210,7 +271,8 @@ def rgx_get_bvh(h, n, stream=None):
     perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     nodes = torch.empty(max(n - 1, 1), 16, dtype=torch.float32, device=dev)
     root = torch.empty(6, dtype=torch.float32, device=dev)
-    _check(lib().rgx_get_bvh(h, _ptr(codes), _ptr(perm), _ptr(nodes), _ptr(root), _stream(stream)), h)
+    _check(lib().rgx_get_bvh(h, _ptr(codes, dtype=torch.int64), _ptr(perm, dtype=torch.int32), _ptr(nodes),
+                             _ptr(root), _stream(stream)), h)
     return codes[:n], perm[:n], nodes, root
 
 
@@ -225,10 +287,15 @@ def rgx_autotune(h, cams: Cameras, base, tune_ns, with_backward, rgba, state, d_
     """Returns (best RgxOpts, best time in ms).  `grads` are scratch buffers."""
     best = RgxOpts()
     ms = C.c_float(0.0)
+    R = cams.n_rays
     g = grads if grads is not None else [None] * 5
+    _same_device(rgba, state, d_rgba, *g)
+    p_rgba = _ptr(rgba, "rgba", 4 * R, optional=False)
+    p_state = _ptr(state, "fwd_state", dtype=None, nbytes=_state_bytes(cams), optional=False)
+    p_d = _ptr(d_rgba, "d_rgba", 4 * R, optional=not with_backward)
+    p_g = [_ptr(x, "gradient scratch", optional=not with_backward) for x in g]
     _check(lib().rgx_autotune(h, cams.ptr, cams.count, C.byref(base), int(tune_ns), int(with_backward),
-                              _ptr(rgba), _ptr(state), _ptr(d_rgba), *[_ptr(x) for x in g], C.byref(best),
-                              C.byref(ms), _stream(stream)), h)
+                              p_rgba, p_state, p_d, *p_g, C.byref(best), C.byref(ms), _stream(stream)), h)
     return best, float(ms.value)
 
 
@@ -236,22 +303,34 @@ def rgx_morton_sort_noalloc(means, wide, codes, perm, stream=None):
     """Sorted Morton codes / permutation of `means` with no device allocation
     (static scratch, n <= 262144).  codes: int64 [n] (uint64 bits), perm: int32 [n]."""
     n = int(means.shape[0])
-    _check(lib().rgx_morton_sort_noalloc(n, _ptr(means), int(bool(wide)), _ptr(codes), _ptr(perm),
-                                         _stream(stream)))
+    _same_device(means, codes, perm)
+    p_m = _ptr(means, "means", 3 * n)
+    p_c = _ptr(codes, "codes", n, dtype=torch.int64)
+    p_p = _ptr(perm, "perm", n, dtype=torch.int32)
+    _check(lib().rgx_morton_sort_noalloc(n, p_m, int(bool(wide)), p_c, p_p, _stream(stream)))
 
 
 def rgx_isotropic_loss(scales, r0, weight, loss, d_scales, stream=None):
     """loss (device float [1]) += weight * L_s; d_scales += weight * dL_s/ds (Eqs. 6-8)."""
-    _check(lib().rgx_isotropic_loss(int(scales.shape[0]), _ptr(scales), float(r0), float(weight), _ptr(loss),
-                                    _ptr(d_scales), _stream(stream)))
+    n = int(scales.shape[0])
+    _same_device(scales, loss, d_scales)
+    p_s = _ptr(scales, "scales", 3 * n)
+    p_l = _ptr(loss, "loss", 1)
+    p_g = _ptr(d_scales, "d_scales", 3 * n)
+    _check(lib().rgx_isotropic_loss(n, p_s, float(r0), float(weight), p_l, p_g, _stream(stream)))
 
 
 def rgx_densify_accumulate(means, d_means, cams: Cameras, stat, count, stream=None):
     """Eq. 11 statistic of one view (cams holds exactly one camera)."""
     if cams.count != 1:
         raise ValueError("one camera per call")
-    _check(lib().rgx_densify_accumulate(int(means.shape[0]), _ptr(means), _ptr(d_means), cams.ptr, _ptr(stat),
-                                        _ptr(count), _stream(stream)))
+    n = int(means.shape[0])
+    _same_device(means, d_means, stat, count)
+    p_m = _ptr(means, "means", 3 * n)
+    p_d = _ptr(d_means, "d_means", 3 * n)
+    p_s = _ptr(stat, "stat", n)
+    p_c = _ptr(count, "count", n, dtype=torch.int32)
+    _check(lib().rgx_densify_accumulate(n, p_m, p_d, cams.ptr, p_s, p_c, _stream(stream)))
 
 
 # ------------------------------------------------------------------ convenience
@@ -262,6 +341,7 @@ class Scene:
         self.device = torch.cuda.current_device() if device is None else int(device)
         self.h = rgx_scene_create(self.device)
         self.n = 0
+        self.sh_degree = 3
         self._keep = None
 
     def __del__(self):
@@ -273,8 +353,12 @@ class Scene:
             pass
 
     def build(self, means, scales, quats, densities, sh, opts, sh_degree: int = 3, stream=None):
-        self.n = int(means.shape[0])
+        for t in (means, scales, quats, densities, sh):
+            if isinstance(t, torch.Tensor) and t.is_cuda and t.device.index != self.device:
+                raise ValueError(f"parameters on {t.device}, scene on cuda:{self.device}")
         rgx_build_bvh(self.h, means, scales, quats, densities, sh, sh_degree, opts, stream)
+        self.n = int(means.shape[0])
+        self.sh_degree = int(sh_degree)
 
     def forward(self, cams: Cameras, opts, want_state: bool = True, stream=None, sched_cap: int = 0):
         dev = torch.device("cuda", self.device)
@@ -291,7 +375,8 @@ class Scene:
 
     def backward(self, cams: Cameras, opts, state, d_rgba, grads, stream=None):
         self._keep = cams
-        rgx_render_backward(self.h, cams, opts, state, d_rgba, *grads, stream=stream)
+        rgx_render_backward(self.h, cams, opts, state, d_rgba, *grads, stream=stream, n=self.n,
+                            sh_degree=self.sh_degree)
 
     def status(self, stream=None) -> int:
         return rgx_sync_status(self.h, stream)
