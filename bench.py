@@ -48,6 +48,12 @@ STEP_WORKLOADS = {
 METRIC = "Mrays/s render & fwd+bwd ms/iter vs plain marcher at ≤1e-4 err; % HBM peak"
 
 
+def workload_label(name: str, fallback: str = "") -> str:
+    """The config's workload string; both arms (the CUDA path and the oracle)
+    print the same one for the same workload."""
+    return f"{name}: " + STEP_WORKLOADS.get(name, fallback)
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -576,8 +582,8 @@ def main():
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic",
-               "config": {"workload": f"{args.workload}: " + STEP_WORKLOADS.get(
-                   args.workload, f"{w.scene.n} Gaussians, first of {len(w.cameras)} views"),
+               "config": {"workload": workload_label(args.workload,
+                                                     f"{w.scene.n} Gaussians, first of {len(w.cameras)} views"),
                           "sample": f"{len(pix)} seeded pixels of the {cam.width}x{cam.height} view per step"},
                "cpu_baseline": {"value": v, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
                                 "sample": f"{len(pix)} seeded pixels per step, forward"
@@ -622,8 +628,8 @@ def main():
         "metric": METRIC, "value": r["value"], "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: " + STEP_WORKLOADS[args.workload] +
-                               " (tile shape and hit_cap from rgx_autotune unless fixed)",
+        "config": {"workload": workload_label(args.workload),
+                   "knobs": "tile shape and hit_cap from rgx_autotune unless fixed",
                    "rays_per_step_per_gpu": r["R"], "l2": "flushed (256 MiB write) between steps",
                    "parallelism": f"{world} independent views, no data-path collective",
                    "autotuned": r["tuned"]},

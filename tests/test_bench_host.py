@@ -58,3 +58,26 @@ def test_profiled_traffic_is_keyed_on_workload_kernel_and_source_hash(monkeypatc
     assert bench.profiled_traffic("k_march<16,1>", "plain_2k") is None
     # counters taken on another source version do not count
     assert bench.profiled_traffic("k_march<16,0>", "outdoor_3m") is None
+
+
+def test_reference_arm_prints_the_contract_line_on_the_host():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores and
+    prints one JSON line with the same metric, unit and workload as the CUDA
+    arm, its own cpu_baseline and an e2e object with no device copies."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "plain_2k",
+                          "--steps", "1", "--warmup", "1"], cwd=root, capture_output=True, text=True,
+                         timeout=600, check=True).stdout.strip().splitlines()
+    d = json.loads(out[-1])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == "Mrays/s" and d["higher_is_better"] is True
+    assert d["config"]["workload"] == bench.workload_label("plain_2k")
+    assert d["steps"] == 1 and d["warmup"] == 1 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["dtype"] == "f64" and d["data"] == "synthetic"
