@@ -335,35 +335,82 @@ def run_rgx(args, rank, world, local):
     torch.cuda.synchronize()
     n_touched = touched_gaussians(grads)
 
-    # e2e through the C-ABI with host buffers: H2D params + upstream, D2H grads + rgba
+    # e2e through the C-ABI with host buffers: every step uploads its parameters and upstream
+    # gradient from pinned host memory and downloads its gradients and image.  The copies run
+    # on a copy stream with two buffer slots, so step i+1's upload and step i's download overlap
+    # the kernels of the neighbouring steps; the timed region runs from before the first upload
+    # to after the last download.
     host_in = [x.cpu().pin_memory() for x in t] + [upstream.cpu().pin_memory()]
-    host_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in t] + \
-               [torch.empty(R, 4, dtype=torch.float32, pin_memory=True)]
-    dev_in = [torch.empty_like(x) for x in t] + [torch.empty_like(upstream)]
+    cs = torch.cuda.Stream(device=dev)
+    slots = [dict(dev_in=[torch.empty_like(x) for x in t] + [torch.empty_like(upstream)],
+                  grads=[torch.empty_like(x) for x in t],
+                  rgba=torch.empty(R, 4, dtype=torch.float32, device=dev), state=rgx.new_state(R, dev),
+                  host_out=[torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in t] +
+                           [torch.empty(R, 4, dtype=torch.float32, pin_memory=True)],
+                  loaded=torch.cuda.Event(), computed=torch.cuda.Event(), unloaded=torch.cuda.Event(),
+                  used=False) for _ in range(2)]
     h2d = sum(x.numel() * x.element_size() for x in host_in)
-    d2h = sum(x.numel() * x.element_size() for x in host_out)
+    d2h = sum(x.numel() * x.element_size() for x in slots[0]["host_out"])
+    n_g = int(t[0].shape[0])
 
-    def e2e_step():
-        for d, h in zip(dev_in, host_in):
-            d.copy_(h, non_blocking=True)
-        sc.build(*dev_in[:5], opts)
-        rgba_, state_ = sc.forward(cams, opts)
-        gl = [torch.zeros_like(x) for x in dev_in[:5]]
-        sc.backward(cams, opts, state_, dev_in[5], gl)
-        for h, d in zip(host_out, gl + [rgba_]):
-            h.copy_(d, non_blocking=True)
+    def upload(sl):
+        with torch.cuda.stream(cs):
+            if sl["used"]:
+                cs.wait_event(sl["computed"])  # the slot's previous step has consumed its inputs
+            for d, h in zip(sl["dev_in"], host_in):
+                d.copy_(h, non_blocking=True)
+            sl["loaded"].record(cs)
 
-    for _ in range(2):
-        e2e_step()
+    def compute(sl):
+        stream.wait_event(sl["loaded"])
+        if sl["used"]:
+            stream.wait_event(sl["unloaded"])  # the slot's previous results have left the device
+        d = sl["dev_in"]
+        rgx.rgx_build_bvh(sc.h, *d[:5], 3, opts, stream=stream)
+        rgx.rgx_render_forward(sc.h, cams, opts, sl["rgba"], sl["state"], stream=stream)
+        for g in sl["grads"]:
+            g.zero_()
+        rgx.rgx_render_backward(sc.h, cams, opts, sl["state"], d[5], *sl["grads"], stream=stream, n=n_g)
+        sl["computed"].record(stream)
+        sl["used"] = True
+
+    def download(sl):
+        with torch.cuda.stream(cs):
+            cs.wait_event(sl["computed"])
+            for h, d in zip(sl["host_out"], sl["grads"] + [sl["rgba"]]):
+                h.copy_(d, non_blocking=True)
+            sl["unloaded"].record(cs)
+
+    def e2e_run(nsteps, e0=None, e1=None):
+        if e0 is not None:
+            e0.record(stream)
+        cs.wait_stream(stream)
+        upload(slots[0])
+        for i in range(nsteps):
+            if i + 1 < nsteps:
+                upload(slots[(i + 1) % 2])
+            compute(slots[i % 2])
+            download(slots[i % 2])
+        stream.wait_event(slots[(nsteps - 1) % 2]["unloaded"])
+        if e1 is not None:
+            e1.record(stream)
+        return slots[(nsteps - 1) % 2]["host_out"]
+
+    e2e_run(2)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
+    last = e2e_run(args.steps, e0, e1)
     barrier()
     e2e_ms = e0.elapsed_time(e1) / args.steps
+    # the downloaded results are the step's: the image bit for bit, the gradients (float
+    # atomics, summation order free) to rounding
+    if not torch.equal(last[5], rgba.cpu()):
+        raise RuntimeError("end-to-end image differs from the device-resident step's")
+    for h, g in zip(last[:5], grads):
+        ref = g.cpu()
+        if float((h - ref).norm()) > 1e-4 * max(float(ref.norm()), 1e-30):
+            raise RuntimeError("end-to-end gradients differ from the device-resident step's")
 
     # the plain single-view marcher on the same GPU (uniform step = dt_min, no skip,
     # caller-order storage, scanline rays): forward and forward+adjoint
@@ -403,7 +450,9 @@ def run_rgx(args, rank, world, local):
     return dict(R=R, ms_per_step=ms_per_step, value=value, build_ms=statistics.median(build_ms),
                 fwd_ms=statistics.median(fwd_ms), bwd_ms=statistics.median(bwd_ms), wall_s=wall,
                 e2e=dict(value=whole_job_mrays(world, R, 1, e2e_ms), unit="Mrays/s", h2d_bytes_per_step=h2d,
-                         d2h_bytes_per_step=d2h, ms_per_step=e2e_ms),
+                         d2h_bytes_per_step=d2h, ms_per_step=e2e_ms,
+                         copies="pinned host buffers; uploads and downloads on a copy stream, two buffer "
+                                "slots, overlapping the neighbouring steps' kernels"),
                 counters_fwd=cf, counters_bwd=cb, clocks=clocks, status=st, plain=plain, opts=w.options, tuned=tuned,
                 n=w.scene.n, n_touched=n_touched, steps_launches=launches_per_step(w.options) * args.steps)
 
