@@ -170,17 +170,19 @@ def touched_gaussians(grads) -> int:
     return int(torch.cat([g.reshape(n, -1) for g in grads], 1).ne(0).any(1).sum())
 
 
-def hbm_roofline(n_touched: int, rays: int, seconds: float, backward: bool, peak_gbs: float, traffic=None):
+def hbm_roofline(n_touched: int, rays: int, seconds: float, backward: bool, peak_gbs: float, traffic=None,
+                 ray_bytes: int = 32):
     """Algorithmic HBM bytes of one march launch and the bandwidth they imply.
 
     Forward: each touched Gaussian's 236-byte parameter record and one 32-byte
     BVH node per touched Gaussian read once, 16 B RGBA + 16 B state per ray
-    written.  Adjoint: the same reads, 16 B dL/dRGBA + 16 B state per ray, and
-    each touched Gaussian's 236 bytes of gradient read and written once.  Beside
-    them the measured DRAM bytes of the same kernel (ncu), when known.
+    written (`ray_bytes` = 16 for a forward that keeps no state).  Adjoint: the
+    same reads, 16 B dL/dRGBA + 16 B state per ray, and each touched Gaussian's
+    236 bytes of gradient read and written once.  Beside them the measured DRAM
+    bytes of the same kernel (ncu), when known.
     """
     per_g = 236 + 32 + (2 * 236 if backward else 0)
-    alg = n_touched * per_g + rays * 32
+    alg = n_touched * per_g + rays * ray_bytes
     out = {"algorithmic_bytes": alg, "achieved": alg / seconds / 1e9, "peak": peak_gbs, "unit": "GB/s",
            "frac": alg / seconds / 1e9 / peak_gbs, "touched_gaussians": n_touched}
     if traffic is not None:
@@ -582,6 +584,12 @@ def run_sweep(args):
     ms_per_view_total = sum(x[2] for x in per_view)
     fps = sorted(((wd * ht, 1e3 / ms) for wd, ht, ms in per_view))
     q = [fps[0], fps[len(fps) // 2], fps[-1]]
+    # forward only: no gradient tells which Gaussians were read, so all of them count (an upper bound)
+    peaks, src = load_peaks()
+    hbm = hbm_roofline(w.scene.n, cams_all.n_rays, ms_persistent / 1e3, False, float(peaks.get("hbm_gbs", 6400.0)),
+                       ray_bytes=16)
+    hbm.update(kernel="k_march<16,0>", peak_source=f"{src} copy bandwidth",
+               touched_note="every Gaussian counted as read (upper bound; forward only)")
     return {"metric": METRIC, "value": cams_all.n_rays / ms_persistent / 1e3, "unit": "Mrays/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_persistent, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -592,6 +600,7 @@ def run_sweep(args):
             "fps_per_view": {"smallest": {"pixels": q[0][0], "fps": q[0][1]},
                              "median": {"pixels": q[1][0], "fps": q[1][1]},
                              "largest": {"pixels": q[2][0], "fps": q[2][1]}},
+            "hbm_roofline": hbm,
             "device_status": sc.status()}
 
 

@@ -39,6 +39,9 @@ def test_hbm_roofline_counts_the_method_bytes():
     assert np.isclose(b["frac"], b["achieved"] / 6505.6)
     assert np.isclose(b["dram_gbs"], 10.0) and np.isclose(b["dram_frac"], 10.0 / 6505.6)
     assert "dram_bytes" not in f
+    # a forward that keeps no per-ray state writes only RGBA
+    g = bench.hbm_roofline(1000, 64, 1e-3, False, 6505.6, ray_bytes=16)
+    assert g["algorithmic_bytes"] == 1000 * (236 + 32) + 64 * 16
 
 
 def test_profiled_traffic_is_keyed_on_workload_kernel_and_source_hash(monkeypatch, tmp_path):
