@@ -15,6 +15,7 @@ Independent references used here:
 Rays, rotations, chords and SH values are rebuilt here from their definitions
 with scipy, not taken from the oracle.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -307,3 +308,52 @@ def test_segment_limit_is_reported():
     o_ = opts(dt=0.01, max_segments=3)
     r = oracle.render(w.scene, w.cameras[0], o_)
     assert r["n_iter_limit"] > 0
+
+
+# ---------------------------------------------------------------- rays and bounds
+def test_rays_pass_through_the_pixel_they_project_to():
+    """Ray generation pinned by its inverse: projecting any point of pixel (u, v)'s
+    ray back through the camera (world to camera by the inverse of the c2w
+    rotation, perspective division, intrinsics) lands on that pixel's centre
+    (u + 1/2, v + 1/2) in front of the camera; the ray starts at the camera
+    centre and has unit length.  Random rotations, off-centre principal points
+    and unequal focal lengths, so a swapped axis or intrinsic fails."""
+    rng = np.random.default_rng(21)
+    for _ in range(5):
+        rot = Rotation.random(random_state=int(rng.integers(1 << 30))).as_matrix()
+        centre = rng.normal(size=3) * 2
+        c2w = np.concatenate([rot, centre[:, None]], 1).astype(np.float32)
+        W, H = int(rng.integers(5, 40)), int(rng.integers(5, 40))
+        cam = synth.Camera(c2w, float(rng.uniform(20, 80)), float(rng.uniform(20, 80)),
+                           float(rng.uniform(0, W)), float(rng.uniform(0, H)), W, H)
+        R64, C64 = c2w[:, :3].astype(np.float64), c2w[:, 3].astype(np.float64)
+        for pix in rng.integers(0, W * H, size=20):
+            o, d = oracle.ray(cam, int(pix))
+            np.testing.assert_allclose(o, C64, atol=1e-12)
+            assert abs(np.linalg.norm(d) - 1.0) < 1e-12
+            for t in (0.5, 3.0, 40.0):
+                pc = np.linalg.solve(R64, o + t * d - C64)
+                assert pc[2] > 0
+                u = cam.fx * pc[0] / pc[2] + cam.cx
+                v = cam.fy * pc[1] / pc[2] + cam.cy
+                assert abs(u - (pix % W + 0.5)) < 1e-9 and abs(v - (pix // W + 0.5)) < 1e-9
+
+
+@pytest.mark.parametrize("mode", ["uniform", "adaptive_skip"])
+def test_far_bound_at_the_scene_box_exit_changes_nothing(mode):
+    """t_far <= 0 stands for the exit of the scene box (the union of the
+    ellipsoid boxes).  Density is zero outside that box, so an explicit far
+    bound beyond it must give the same render, for a camera outside the box
+    (rays cross the whole sparse scene, so an exit computed too early would cut
+    density off), a camera inside it, and rays that miss it."""
+    w = synth.workload("plain_2k", n=200)
+    o_ = w.options if mode == "uniform" else synth.fast_options(dt_min=0.005, sigma_eps=w.options.sigma_eps)
+    inside = synth.look_at(np.zeros(3), np.array([1.0, 0.3, 0.2]), 60.0, 10, 10)
+    away = synth.look_at(np.array([0.0, 0.0, 3.0]), np.array([0.0, 0.0, 6.0]), 30.0, 6, 6)
+    for cam in (synth.rescale_camera(w.cameras[0], 12 / 64), inside, away):
+        r_far = oracle.render(w.scene, dataclasses.replace(cam, t_far=20.0), o_)
+        r_auto = oracle.render(w.scene, dataclasses.replace(cam, t_far=0.0), o_)
+        np.testing.assert_allclose(r_auto["rgba"], r_far["rgba"], atol=1e-14)
+        if cam is not away:
+            assert (r_auto["rgba"][:, 3] > 1e-3).sum() > cam.n_rays // 4
+    np.testing.assert_array_equal(r_auto["rgba"], np.tile([*o_.bg, 0.0], (away.n_rays, 1)))
