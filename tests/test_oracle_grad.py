@@ -76,3 +76,35 @@ def test_adjoint_matches_central_differences(mode):
         assert rel_l2 < 1e-6, f"{name}: rel L2 {rel_l2:.3g}"
         checked += int(m.sum())
     assert checked > 300
+
+
+def test_clamped_colour_channels_get_no_sh_gradient():
+    """c_l = max(0, 1/2 + sum_k Y_k K_lk) per channel: where a channel is clamped
+    to 0 its SH coefficients do not move the render, so central differences and
+    the adjoint both give exactly zero for them, while the unclamped channels
+    still match central differences."""
+    sc = cluster_scene(n=4, seed=3)
+    sh = sc.sh.copy()
+    sh[:, 0, 1] = -6.0  # green DC far below the offset: green clamped in every direction
+    sc = synth.Scene(sc.means, sc.scales, sc.quats, sc.densities, sh, 3)
+    cam = synth.look_at(np.array([0.2, -0.4, 1.6]), np.zeros(3), 22.0, 5, 5)
+    o_ = synth.Options(dt=0.004, n_s=8, t_eps=0.0, sigma_eps=SIG_EPS)
+    W = np.random.default_rng(8).normal(size=(cam.n_rays, 4))
+    base = oracle.render(sc, cam, o_, sched_cap=512)
+    assert np.all(base["rgba"][:, 1] == 0.0) and base["rgba"][:, 0].max() > 0.05
+    g = oracle.backward(sc, cam, o_, W)["sh"]
+    np.testing.assert_array_equal(g[:, :, 1], 0.0)
+    assert np.abs(g[:, :, 0]).max() > 1e-4
+    rng = np.random.default_rng(0)
+    for _ in range(12):
+        l, k, c = int(rng.integers(4)), int(rng.integers(16)), int(rng.integers(2))
+        h = 1e-6
+        vals = []
+        for sgn in (1, -1):
+            pert = sh.copy()
+            pert[l, k, c] += sgn * h
+            L, _ = _loss(synth.Scene(sc.means, sc.scales, sc.quats, sc.densities, pert, 3), cam, o_, W,
+                         base["sched"], base["sched_n"])
+            vals.append(L)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g[l, k, c]) <= 1e-6 * max(1.0, abs(g[:, :, 0]).max())

@@ -260,6 +260,82 @@ def test_adaptive_step_special_cases():
                 assert r["sched"][p, s, 1] >= r["sched"][p, s, 0] / beta * (1 - 1e-15)
 
 
+def test_adaptive_step_follows_transmittance():
+    """Eq. 5 away from T = 1: for every evaluated segment i the step is
+    min(max(t_S,i / beta, dt_min) * T_i^(-1/3), dt_max), with T_i the
+    transmittance at the segment's start, read by replaying the ray's first i
+    segments.  The scene is dense enough that T falls well below 1 and dt_max
+    is wide enough that the T factor is not clamped away."""
+    w = synth.workload("plain_2k", n=400)
+    sc = synth.Scene(w.scene.means, w.scene.scales, w.scene.quats, w.scene.densities * 4.0, w.scene.sh, 3)
+    cam = synth.rescale_camera(w.cameras[0], 16 / 64)
+    o_ = opts(adaptive=True, skip=True, dt_min=0.004, dt_max=0.5, beta=200.0, t_eps=1e-4)
+    r = oracle.render(sc, cam, o_, sched_cap=256)
+    n = r["sched_n"]
+    checked, low_T = 0, 0
+    for i in range(1, 12):
+        idx = np.nonzero(n > i)[0]
+        if idx.size == 0:
+            continue
+        rr = oracle.render(sc, cam, o_, pix=idx, sched=r["sched"][idx], sched_n=np.full(idx.size, i))
+        T = rr["state"][:, 3]
+        tS, dtk = r["sched"][idx, i, 0], r["sched"][idx, i, 1]
+        want = np.minimum(np.maximum(tS / o_.beta, o_.dt_min) * T ** (-1.0 / 3.0), o_.dt_max)
+        np.testing.assert_allclose(dtk, want, rtol=1e-12)
+        checked += idx.size
+        low_T += int((T < 0.7).sum())
+    assert checked > 200 and low_T > 50
+
+
+def test_skipping_jumps_the_gap_between_two_gaussians():
+    """After the last segment touching one Gaussian, an empty segment sends the
+    march to ClosestHit of its end: with adaptive steps the next evaluated
+    segment starts exactly at the second Gaussian's chord entry, and with the
+    uniform lattice one step of guard below it.  Chord ends come from the erf
+    helper's closed-form quadratic, not from the oracle."""
+    s1, s2 = one_gaussian_scene(seed=1, center=(0, 0, 0.6)), one_gaussian_scene(seed=2, center=(0, 0, -0.6))
+    sc = synth.Scene(np.concatenate([s1.means, s2.means]), np.concatenate([s1.scales, s2.scales]),
+                     np.concatenate([s1.quats, s2.quats]), np.concatenate([s1.densities, s2.densities]) * 0.2,
+                     np.concatenate([s1.sh, s2.sh]), 3)
+    cam = camera_at([0.01, 0.02, 3.0], w=6, h=6, fov=2.0)
+    oa = opts(adaptive=True, skip=True, dt_min=0.005, dt_max=0.02, t_eps=0.0)
+    ou = opts(dt=0.01, skip=True, t_eps=0.0)
+    ra, ru = oracle.render(sc, cam, oa, sched_cap=256), oracle.render(sc, cam, ou, sched_cap=256)
+    n = 0
+    for p in range(cam.n_rays):
+        o, d = pinhole_ray(cam, p)
+        c = [gauss_line_integral(sc.means[l], sc.scales[l], sc.quats[l], sc.densities[l], o, d)[1] for l in (0, 1)]
+        if c[0] is None or c[1] is None:
+            continue
+        (a0, a1), (b0, b1) = sorted(c)
+        assert b0 - a1 > 0.2
+        n += 1
+        starts = ra["sched"][p, :ra["sched_n"][p], 0]
+        after = starts[starts > a1]
+        assert after.size and after[0] == pytest.approx(b0, abs=1e-9)
+        su = ru["sched"][p, :ru["sched_n"][p], 0]
+        after_u = su[su > a1]
+        assert after_u.size and b0 - 2 * ou.dt - 1e-9 <= after_u[0] <= b0 - ou.dt + 1e-9
+    assert n > 10
+
+
+def test_skipping_from_inside_a_gaussian():
+    """A camera inside a Gaussian's support: ClosestHit(t_n) is t_n itself (the
+    enclosing chord already contains it), so the first segment starts at t_n,
+    and the skipping render equals the plain one within T_eps * max c."""
+    sc = one_gaussian_scene(sig=3.0, scale=0.5)
+    cam = camera_at([0.05, 0.02, 0.1], target=(1, 0.3, 0.2), w=8, h=8, fov=40.0)
+    o_ = opts(adaptive=True, skip=True, dt_min=0.005, dt_max=0.02)
+    r = oracle.render(sc, cam, o_, sched_cap=64)
+    assert np.all(r["sched_n"] > 0)
+    np.testing.assert_array_equal(r["sched"][:, 0, 0], cam.t_near)
+    ou, ou_skip = opts(dt=0.01), opts(dt=0.01, skip=True)
+    r0, r1 = oracle.render(sc, cam, ou), oracle.render(sc, cam, ou_skip)
+    assert r0["rgba"][:, 3].min() > 0.05
+    cmax = 0.5 + np.abs(sc.sh).sum(axis=1).max()
+    assert np.abs(r0["rgba"] - r1["rgba"]).max() <= ou.t_eps * cmax + 1e-12
+
+
 def test_closest_hit_starts_at_first_chord_entry():
     sc = one_gaussian_scene()
     cam = camera_at([0.3, -1.2, 1.5])
