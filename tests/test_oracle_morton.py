@@ -33,6 +33,41 @@ def test_interleave_locality_and_bijection():
             assert shared // 3 == k
 
 
+def test_interleave_bit_order_by_hand():
+    """Bit order of the interleave (reading R17): within each 3-bit group x is
+    the most significant, then y, then z, lowest group from bit 0.  Codes
+    worked out by hand: (1,0,0) -> 0b100, (0,1,0) -> 0b010, (0,0,1) -> 0b001,
+    (2,0,0) -> 0b100000, (3,1,2) -> x=11 y=01 z=10 -> groups (x1 y1 z1)(x0 y0 z0)
+    = (1 0 1)(1 1 0) = 0b101110, and the top cell (2^b - 1 on every axis) ->
+    3b ones."""
+    for bits in (10, 21):
+        cells = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [2, 0, 0], [3, 1, 2],
+                          [(1 << bits) - 1] * 3], dtype=np.uint64)
+        want = [0b100, 0b010, 0b001, 0b100000, 0b101110, (1 << (3 * bits)) - 1]
+        assert [int(c) for c in morton.interleave(cells, bits)] == want
+
+
+def test_order_is_stable_and_exact_on_63_bit_codes():
+    """order() sorts by (code, original index) (reading R13): equal codes keep
+    their input order, and 63-bit codes compare as exact integers (checked
+    against Python's integer sort of (code, index) pairs)."""
+    rng = np.random.default_rng(5)
+    base = rng.normal(size=(300, 3)).astype(np.float32)
+    means = base[rng.integers(0, 300, size=2000)]  # many exact duplicates -> equal codes
+    for wide in (False, True):
+        c, perm = morton.order(means, wide)
+        raw = morton.codes(means, wide)
+        want = sorted(range(len(raw)), key=lambda i: (int(raw[i]), i))
+        assert perm.tolist() == want
+        assert [int(x) for x in c] == [int(raw[i]) for i in want]
+    # distinct 63-bit codes closer together than float64 can tell apart
+    m = np.zeros((3, 3), dtype=np.float32)
+    m[:, 0] = [1.0, np.nextafter(np.float32(1.0), np.float32(0.0)), 0.0]
+    m[2, 1] = 1.0
+    c, perm = morton.order(m, True)
+    assert all(int(c[i]) <= int(c[i + 1]) for i in range(len(c) - 1))
+
+
 def test_quantisation_matches_exact_except_at_boundaries():
     rng = np.random.default_rng(1)
     m = rng.normal(size=(20000, 3)).astype(np.float32)
