@@ -1,7 +1,8 @@
 """BVH build parity (integer work: bit-exact) and box conservativeness.
 
 * sorted Morton codes and the permutation equal the oracle's float32
-  quantisation + stable sort (30- and 63-bit codes);
+  quantisation + stable sort (30- and 63-bit codes), also when many
+  Gaussians share a code;
 * every internal node's (first, split, last) equals the radix tree of the
   sorted codes;
 * every leaf box contains its Gaussian's sigma_eps ellipsoid (oracle FP64
@@ -39,6 +40,27 @@ def test_codes_perm_and_tree_bit_exact(name, n, wide):
     first, last, split = lbvh.radix_tree(ref_codes)
     nn = len(first)
     ints = nodes[:nn].view(np.int32)
+    np.testing.assert_array_equal(ints[:, 3], first)
+    np.testing.assert_array_equal(ints[:, 7], split)
+    np.testing.assert_array_equal(ints[:, 11], last)
+
+
+@pytest.mark.parametrize("wide", [False, True])
+def test_equal_codes_keep_index_order_and_split_by_position(wide):
+    """Many Gaussians at exactly the same mean share one Morton code: the sort
+    must keep them in caller order and the radix tree must split the run of
+    equal codes by sorted position, as the oracle's (code, index) keys do."""
+    w = synth.workload("plain_2k")
+    rng = np.random.default_rng(9)
+    pick = rng.integers(0, 300, size=w.scene.n)
+    sc = synth.Scene(w.scene.means[pick], w.scene.scales, w.scene.quats, w.scene.densities, w.scene.sh, 3)
+    codes, perm, nodes, _ = build(sc, synth.fast_options(morton63=wide))
+    ref_codes, ref_perm = morton.order(sc.means, wide=wide)
+    assert len(np.unique(ref_codes)) < sc.n // 2
+    np.testing.assert_array_equal(codes, ref_codes)
+    np.testing.assert_array_equal(perm, ref_perm)
+    first, last, split = lbvh.radix_tree(ref_codes)
+    ints = nodes[:len(first)].view(np.int32)
     np.testing.assert_array_equal(ints[:, 3], first)
     np.testing.assert_array_equal(ints[:, 7], split)
     np.testing.assert_array_equal(ints[:, 11], last)
