@@ -64,3 +64,22 @@ def test_outdoor_gradients_sampled():
     cam = w.cameras[0]
     pix = synth.pixel_subset(cam, 512, seed=9)
     run_case(w.scene, cam, w.options, pix, sched_cap=96, params=oracle.Params(w.scene))
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_lower_sh_degrees_forward_and_gradients(deg):
+    """sh_degree 0..2 (1, 4, 9 coefficients per channel): the CUDA path packs,
+    colours and differentiates only the first (deg+1)^2 coefficients; image
+    and gradients match the oracle of the same degree."""
+    from helpers import TOL_RGBA, compare_rgba
+    w = synth.workload("plain_2k", n=600)
+    nk = (deg + 1) ** 2
+    sc = synth.Scene(w.scene.means, w.scene.scales, w.scene.quats, w.scene.densities,
+                     np.ascontiguousarray(w.scene.sh[:, :nk, :]), deg)
+    cam = w.cameras[0]
+    r = gpu_render(sc, [cam], w.options)
+    assert r["status"] == 0
+    err, ndiv = compare_rgba(r["rgba"], cam, sc, w.options)
+    assert err <= TOL_RGBA and ndiv == 0
+    errs = run_case(sc, cam, w.options, np.arange(cam.n_rays))
+    assert all(e <= TOL_GRAD for e in errs.values())
