@@ -93,3 +93,21 @@ def test_batched_views_sampled(name, per_cam, ncam_checked):
         err, _ = compare_rgba(r["rgba"][sl], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"][sl],
                               gpu_sched_n=r["sched_n"][sl], max_divergent_frac=0.05, params=params)
         assert err <= TOL_RGBA
+
+
+@pytest.mark.parametrize("fast", [False, True])
+def test_explicit_near_and_far_bounds(fast):
+    """Camera t_near > 0 and t_far > 0 (Algorithm 1's t_n, t_f given by the
+    caller rather than the scene box): the march covers exactly [t_n, t_f) and
+    cuts the scene at both ends, as the oracle does."""
+    import dataclasses
+    w = synth.workload("plain_2k")
+    cam = dataclasses.replace(w.cameras[0], t_near=2.6, t_far=3.4)
+    o = synth.fast_options(dt=0.01) if fast else w.options
+    r = gpu_render(w.scene, [cam], o, sched_cap=64)
+    assert r["status"] == 0
+    err, _ = compare_rgba(r["rgba"], cam, w.scene, o, gpu_sched=r["sched"], gpu_sched_n=r["sched_n"],
+                          max_divergent_frac=0.01)
+    assert err <= TOL_RGBA
+    full = gpu_render(w.scene, w.cameras, o)
+    assert np.abs(full["rgba"] - r["rgba"]).max() > 0.05  # the bounds really cut density off
