@@ -89,7 +89,10 @@ typedef struct {
     float bg[3];                 /* background colour, added as T_final * bg */
     int32_t tile_w, tile_h;      /* ray tile, tile_w * tile_h == 32 (ZTILES only) */
     int32_t hit_cap;             /* chord-list capacity per ray (multiple of 32, 32..1024); never drops hits */
-    int32_t max_segments;        /* loop bound per ray; 0 = derived from the ray length */
+    int32_t max_segments;        /* loop bound per ray; 0 = derived from the ray length: (t_f - t_n) / dt
+                                    (uniform) or / (N_S dt_min) (Eq. 5), plus 8, at most 2e9.  A scene box
+                                    vast next to the step (say one Gaussian of enormous scale) then lets
+                                    every ray march that far: give max_segments or t_far to bound the work */
 } rgx_opts;
 
 /* Create / destroy a scene handle bound to CUDA device `device`. */
