@@ -101,7 +101,7 @@ rgx_status rgx_scene_destroy(rgx_scene* scene);
 
 /*
  * Build the acceleration structure and packed parameters for n Gaussians.
- * Sec. 3.2 ("the structure is updated at each optimization step") and Sec.
+ * Sec. 3.2 (the BVH is rebuilt at every optimisation step) and Sec.
  * 3.3 (Z-order re-indexing); ellipsoid AABB from Supp. Sec. 2.2.
  *
  *   means      [n,3]            Gaussian means mu

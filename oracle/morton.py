@@ -2,10 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Sec. 3.3 ("Enhancing Memory Access Efficiency through Spatial Reordering of
-Gaussians"): the mean of each Gaussian is normalised to the scene box,
-quantised to integers and mapped to a Z-order index; Gaussians are sorted by
-it.  The quantisation is a floating-point decision that produces an integer,
+Sec. 3.3 (memory reordering of the Gaussians): the mean of each Gaussian is
+normalised to the scene box and quantised to integer cells whose bits are
+interleaved into a Z-order index; Gaussians are sorted by it.  The quantisation is a floating-point decision that produces an integer,
 so it is taken here in the same precision as the kernel (IEEE float32, each
 operation rounded to nearest, no fused multiply-add):
 

@@ -2,7 +2,7 @@
 //
 // Algorithm 1 leaves three implementation knobs open: the number of samples
 // per segment N_S, the capacity of the hit-primitive buffer H_b, and (Sec.
-// 3.3, "Improving Ray Coherence") the shape of the 2D ray tiles.  The best
+// 3.3, ray coherence) the shape of the 2D ray tiles.  The best
 // values depend on the scene's depth complexity and on the cameras, so they
 // are measured: every candidate configuration is run on the caller's actual
 // scene and cameras and timed with CUDA events on the caller's stream.

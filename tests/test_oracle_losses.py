@@ -5,10 +5,10 @@
   Carlo over rotations, exact AABB from the rotated axes) and is approached
   by the worst rotation; it equals 6/pi for isotropic Gaussians;
 * the loss vanishes below r0 and its gradient matches central differences;
-* the densification weight alpha |grad mu| equals the norm of the gradient
-  with respect to the mean projected on the sphere of radius f around the
-  camera (Supp. Sec. 3), for tangential gradients -- checked by
-  differentiating through the projection numerically.
+* the densification weight alpha |grad mu| equals the norm of the loss's
+  derivative by the image of the mean on a radius-f sphere centred at the
+  camera (Supp. Sec. 3), when the gradient is tangential -- checked by
+  differentiating through that central projection numerically.
 """
 import math
 
