@@ -121,6 +121,43 @@ def test_single_gaussian_erf_closed_form(mode):
     assert nhit > cam.n_rays // 3
 
 
+def test_explicit_bounds_integrate_only_between_them():
+    """Algorithm 1 integrates over [t_n, t_f) only: with t_near and t_far cutting
+    one Gaussian's chord at 10 % and 50 % of its length, the opacity is
+    1 - exp(-tau) of the erf closed form taken between those two bounds, to
+    within the one midpoint cell the far bound can split (density at t_f x dt/2)."""
+    sc = one_gaussian_scene(seed=6)
+    cam0 = camera_at([0.3, -1.2, 1.5], w=6, h=6)
+    o_ = opts(dt=5e-5, n_s=16, t_eps=0.0)
+    n = 0
+    for p in range(cam0.n_rays):
+        o, d = pinhole_ray(cam0, p)
+        tau, ch = gauss_line_integral(sc.means[0], sc.scales[0], sc.quats[0], sc.densities[0], o, d)
+        if ch is None or ch[1] - ch[0] < 0.02:
+            continue
+        t0 = ch[0] + 0.1 * (ch[1] - ch[0])
+        t1 = ch[0] + 0.5 * (ch[1] - ch[0])
+        cam = dataclasses.replace(cam0, t_near=float(t0), t_far=float(t1))
+        tn, tf = float(np.float32(t0)), float(np.float32(t1))  # the camera stores float32 bounds
+        r = oracle.render(sc, cam, o_, pix=np.array([p]))
+        # partial integral: same q(t) = a (t - t_c)^2 + q_min as the whole-chord closed form
+        R = Rotation.from_quat([sc.quats[0][1], sc.quats[0][2], sc.quats[0][3], sc.quats[0][0]]).as_matrix()
+        Minv = np.diag(1.0 / np.asarray(sc.scales[0], np.float64)) @ R.T
+        y0, yd = Minv @ (o - sc.means[0]), Minv @ d
+        a = yd @ yd
+        tc = -(y0 @ yd) / a
+        qmin = (y0 + tc * yd) @ (y0 + tc * yd)
+        k = math.sqrt(a / 2)
+        part = sc.densities[0] * math.exp(-qmin / 2) * math.sqrt(math.pi / (2 * a)) * \
+            (erf(k * (tf - tc)) - erf(k * (tn - tc)))
+        assert 0.2 * tau < part < 0.55 * tau  # the bounds really cut the integral
+        # midpoint cells start at t_n; the last counted one ends within dt/2 of t_f
+        g_f = sc.densities[0] * math.exp(-(a * (tf - tc) ** 2 + qmin) / 2)
+        assert r["rgba"][0, 3] == pytest.approx(1 - math.exp(-part), abs=g_f * o_.dt / 2 + 2e-6)
+        n += 1
+    assert n > 5
+
+
 def test_erf_convergence_order():
     sc = one_gaussian_scene(seed=4)
     cam = camera_at([0.0, 0.9, 1.4], w=6, h=6)
