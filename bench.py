@@ -12,9 +12,15 @@ adaptive step + Z-order storage + Z-order ray tiles) + rgx_render_backward
 Prints one JSON line (rank 0).  ``value`` is whole-job Mrays/s of the step
 with inputs resident in HBM, timed with CUDA events per step on the launching
 stream, L2 flushed (256 MiB write) between steps outside the events.
-``e2e`` repeats the step through the same C-ABI with host (pinned) buffers,
-host<->device copies inside the timed region.  ``--impl reference`` times the
-FP64 CPU oracle on the host cores on a bounded pixel sample instead.
+``e2e`` repeats the step through the same C-ABI with host (pinned) buffers:
+every step uploads its parameters and upstream gradient and downloads its
+gradients and image inside the timed region, the copies on a second stream
+overlapping the neighbouring steps' kernels.  ``roofline`` relates the dominant
+kernel's counted FP32/SFU work to the derived ALU peak, ``hbm_roofline`` its
+algorithmic bytes (and the profiled DRAM bytes) to the measured copy bandwidth,
+and ``cpu_baseline`` times the FP64 oracle on all host cores and on one.
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+pixel sample instead.
 Multi-GPU (torchrun): each rank renders its own seeded camera of the same
 scene (weak scaling); ranks share nothing on the data path.
 """
