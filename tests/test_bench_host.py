@@ -84,3 +84,26 @@ def test_reference_arm_prints_the_contract_line_on_the_host():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["dtype"] == "f64" and d["data"] == "synthetic"
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
+    """Launched the way multi-GPU runs are (torchrun, two ranks, 127.0.0.1),
+    the reference arm runs on rank 0 only: exactly one JSON line comes out and
+    both ranks exit 0."""
+    import json
+    import os
+    import socket
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                          "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
+                          "--workload", "plain_2k", "--gpus", "2", "--steps", "1", "--warmup", "1"],
+                         cwd=root, capture_output=True, text=True, timeout=600, check=True)
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
