@@ -19,7 +19,7 @@
  *                                            the renderer (Sec. 3.5) but prints no
  *                                            derivation.
  *
- * Readings where the paper is silent (each is listed in the design notes):
+ * Readings where the paper is silent, ambiguous or leaves a choice open:
  *   - hard truncation per sample: a Gaussian contributes only where
  *     q(x) <= Q_eps = 2 ln(sigma~/sigma_eps);
  *   - samples sit at segment midpoints t_S + (k + 1/2) dt;
