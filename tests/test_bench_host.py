@@ -107,3 +107,18 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_clock_sampler_summarises_rows_and_reasons():
+    """The clocks object of the JSON line: median SM clock under load, the
+    maximum clock, and every throttle reason seen active in any sample."""
+    s = bench.ClockSampler(0)
+    assert s.stop()["reasons"] == ["unsampled"]
+    row = "0, {sm}, 2032, 900.5, 0x0, {hw}, Not Active, Not Active, {cap}"
+    s.rows = [[x.strip() for x in row.format(sm=sm, hw=hw, cap=cap).split(",")]
+              for sm, hw, cap in ((2032, "Not Active", "Not Active"), (1980, "Not Active", "Active"),
+                                  (2032, "Not Active", "Not Active"), ("[N/A]", "Active", "Not Active"))]
+    c = s.stop()
+    assert c["sm_mhz"] == 2032.0 and c["sm_max_mhz"] == 2032.0
+    assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert c["samples"] == 4
