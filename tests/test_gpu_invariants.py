@@ -88,6 +88,29 @@ def test_batch_launch_equals_single_launches():
         off += cam.n_rays
 
 
+def test_batched_adjoint_equals_the_sum_of_single_view_adjoints():
+    # One persistent adjoint launch over several views of uneven size must add
+    # up the per-view gradients (the loss is a sum over views); only the order
+    # of the float atomics differs.
+    w = synth.workload("batch_1m", n=50000, scale_res=0.1)
+    r = gpu_render(w.scene, w.cameras, w.options)
+    d = np.random.default_rng(3).normal(size=r["rgba"].shape)
+    gb = gpu_backward(r, d)
+    assert gb["status"] == 0
+    total = {k: np.zeros_like(gb[k]) for k in ("means", "scales", "quats", "densities", "sh")}
+    off = 0
+    for cam in w.cameras:
+        s = gpu_render(w.scene, [cam], w.options)
+        gs = gpu_backward(s, d[off:off + cam.n_rays])
+        assert gs["status"] == 0
+        for k in total:
+            total[k] += gs[k]
+        off += cam.n_rays
+    for k in total:
+        assert np.abs(total[k]).max() > 0, k
+        np.testing.assert_allclose(gb[k], total[k], rtol=1e-3, atol=1e-4 * np.abs(total[k]).max())
+
+
 def test_empty_scene_and_single_gaussian():
     w = synth.workload("plain_2k")
     bg = (0.2, 0.3, 0.4)
