@@ -68,3 +68,24 @@ def test_struct_layouts_match_the_c_compiler(libpath, tmp_path):
         expect.append(ctypes.sizeof(cls))
         expect += [getattr(cls, f).offset for f, _ in cls._fields_]
     assert vals == expect
+
+
+def test_status_and_flag_constants_match_the_header():
+    """Every RGX_* status code and option flag the binding uses has the value
+    the header defines, and make_opts sets exactly the flags of the options."""
+    from paper_2509_07782_b300 import rgx, synth
+    src = open(HEADER).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(RGX_[A-Z0-9_]+)\s+(\d+)\b", src)}
+    used = {k: getattr(rgx, k) for k in dir(rgx) if k.startswith("RGX_") and isinstance(getattr(rgx, k), int)}
+    assert used and set(used) <= set(defs)
+    for k, v in used.items():
+        assert defs[k] == v, k
+    names = {"skip": "RGX_SKIP", "adaptive": "RGX_ADAPTIVE", "morton": "RGX_MORTON", "ztiles": "RGX_ZTILES",
+             "morton63": "RGX_MORTON63"}
+    for field, flag in names.items():
+        o = synth.Options(**{field: True})
+        assert rgx.make_opts(o).flags == defs[flag], field
+    assert rgx.make_opts(synth.Options()).flags == 0
+    x = rgx.make_opts(synth.fast_options(hit_cap=384, tile_w=16, tile_h=2, max_segments=7, bg=(0.1, 0.2, 0.3)))
+    assert (x.hit_cap, x.tile_w, x.tile_h, x.max_segments) == (384, 16, 2, 7)
+    assert list(x.bg) == pytest.approx([0.1, 0.2, 0.3])
