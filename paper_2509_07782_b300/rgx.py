@@ -17,6 +17,7 @@ read when the stream reaches the copy (``Scene`` keeps the last one alive).
 from __future__ import annotations
 
 import ctypes as C
+import functools
 import os
 import threading
 
@@ -65,6 +66,25 @@ class RgxError(RuntimeError):
 
 _lib = None
 _lock = threading.Lock()
+
+# RGX_NVTX=1: every call that enqueues work opens an NVTX range named after the
+# entry point, so a profiler attributes the kernels it launches to that stage.
+NVTX = os.environ.get("RGX_NVTX", "0") not in ("", "0")
+
+
+def _traced(fn):
+    name = fn.__name__
+
+    @functools.wraps(fn)
+    def call(*args, **kw):
+        if not NVTX:
+            return fn(*args, **kw)
+        torch.cuda.nvtx.range_push(name)
+        try:
+            return fn(*args, **kw)
+        finally:
+            torch.cuda.nvtx.range_pop()
+    return call
 
 
 def lib() -> C.CDLL:
@@ -207,6 +227,7 @@ def _param_ptrs(n, sh_degree, means, scales, quats, densities, sh, prefix=""):
             _ptr(sh, prefix + "sh", nk * 3 * n, optional=not req))
 
 
+@_traced
 def rgx_build_bvh(h, means, scales, quats, densities, sh, sh_degree, opts, stream=None):
     n = int(means.shape[0])
     ptrs = _param_ptrs(n, sh_degree, means, scales, quats, densities, sh)
@@ -217,6 +238,7 @@ def _state_bytes(cams: Cameras) -> int:
     return cams.n_rays * rgx_fwd_state_bytes()
 
 
+@_traced
 def rgx_render_forward(h, cams: Cameras, opts, rgba, state=None, stream=None):
     R = cams.n_rays
     _same_device(rgba, state)
@@ -225,6 +247,7 @@ def rgx_render_forward(h, cams: Cameras, opts, rgba, state=None, stream=None):
     _check(lib().rgx_render_forward(h, cams.ptr, cams.count, C.byref(opts), p_rgba, p_state, _stream(stream)), h)
 
 
+@_traced
 def rgx_render_forward_sched(h, cams: Cameras, opts, rgba, state, sched, sched_n, stream=None):
     R = cams.n_rays
     if sched is None or sched.dim() != 3 or sched.shape[2] != 2:
@@ -239,6 +262,7 @@ def rgx_render_forward_sched(h, cams: Cameras, opts, rgba, state, sched, sched_n
                                           p_n, _stream(stream)), h)
 
 
+@_traced
 def rgx_render_backward(h, cams: Cameras, opts, state, d_rgba, d_means, d_scales, d_quats, d_densities, d_sh,
                         stream=None, n=None, sh_degree: int = 3):
     """`n` (the scene's Gaussian count, when known) and `sh_degree` size-check the
@@ -283,6 +307,7 @@ def rgx_get_counters(h, stream=None):
     return dict(zip(keys, [int(v) for v in out]))
 
 
+@_traced
 def rgx_autotune(h, cams: Cameras, base, tune_ns, with_backward, rgba, state, d_rgba, grads, stream=None):
     """Returns (best RgxOpts, best time in ms).  `grads` are scratch buffers."""
     best = RgxOpts()
@@ -299,6 +324,7 @@ def rgx_autotune(h, cams: Cameras, base, tune_ns, with_backward, rgba, state, d_
     return best, float(ms.value)
 
 
+@_traced
 def rgx_morton_sort_noalloc(means, wide, codes, perm, stream=None):
     """Sorted Morton codes / permutation of `means` with no device allocation
     (static scratch, n <= 262144).  codes: int64 [n] (uint64 bits), perm: int32 [n]."""
@@ -310,6 +336,7 @@ def rgx_morton_sort_noalloc(means, wide, codes, perm, stream=None):
     _check(lib().rgx_morton_sort_noalloc(n, p_m, int(bool(wide)), p_c, p_p, _stream(stream)))
 
 
+@_traced
 def rgx_isotropic_loss(scales, r0, weight, loss, d_scales, stream=None):
     """loss (device float [1]) += weight * L_s; d_scales += weight * dL_s/ds (Eqs. 6-8)."""
     n = int(scales.shape[0])
@@ -320,6 +347,7 @@ def rgx_isotropic_loss(scales, r0, weight, loss, d_scales, stream=None):
     _check(lib().rgx_isotropic_loss(n, p_s, float(r0), float(weight), p_l, p_g, _stream(stream)))
 
 
+@_traced
 def rgx_densify_accumulate(means, d_means, cams: Cameras, stat, count, stream=None):
     """Eq. 11 statistic of one view (cams holds exactly one camera)."""
     if cams.count != 1:

@@ -99,3 +99,22 @@ def test_wrong_dtype_size_or_device_never_reaches_the_library():
     sc.backward(cams, opts, state, torch.randn(R, 4, device="cuda"), good)
     assert sc.status() == 0
     assert np.isfinite(good[0].cpu().numpy()).all()
+
+
+def test_nvtx_ranges_are_opt_in_named_and_balanced(lib_built, monkeypatch):
+    """With RGX_NVTX set, a call opens one NVTX range named after its entry
+    point and closes it even when the call raises; without it, none."""
+    _, cams, opts = _setup()
+    pushed, popped = [], []
+    monkeypatch.setattr(torch.cuda.nvtx, "range_push", lambda name: pushed.append(name))
+    monkeypatch.setattr(torch.cuda.nvtx, "range_pop", lambda: popped.append(1))
+    bad = _host((cams.n_rays, 4))
+    with pytest.raises(ValueError):
+        rgx.rgx_render_forward(None, cams, opts, bad)
+    assert pushed == [] and popped == []
+    monkeypatch.setattr(rgx, "NVTX", True)
+    with pytest.raises(ValueError):
+        rgx.rgx_render_forward(None, cams, opts, bad)
+    with pytest.raises(ValueError):
+        rgx.rgx_isotropic_loss(_host((4, 3)), 10.0, 1.0, _host(1), _host((4, 3)))
+    assert pushed == ["rgx_render_forward", "rgx_isotropic_loss"] and len(popped) == 2
