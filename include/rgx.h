@@ -53,7 +53,7 @@ typedef int32_t rgx_status;
 #define RGX_ERR_WORKSPACE       3   /* device allocation failed */
 #define RGX_ERR_HIT_OVERFLOW    4   /* reserved: hit lists are chunked, never dropped */
 #define RGX_ERR_STACK_OVERFLOW  8   /* device: BVH deeper than the traversal stack */
-#define RGX_ERR_ITER_LIMIT      16  /* device: a ray reached max_segments */
+#define RGX_ERR_ITER_LIMIT      16  /* device: a ray reached max_segments (or the 2^20 default ceiling) */
 #define RGX_ERR_BAD_PARAMS      32  /* device: NaN/Inf parameter, scale <= 0, |q| = 0 */
 #define RGX_ERR_REPLAY          64  /* device: backward replay did not reproduce T_final */
 #define RGX_ERR_NOT_BUILT       128 /* render called before rgx_build_bvh */
@@ -83,17 +83,24 @@ typedef struct {
     int32_t flags;               /* RGX_SKIP | RGX_ADAPTIVE | RGX_MORTON | RGX_ZTILES | RGX_MORTON63 */
     float dt;                    /* uniform step (Eq. 3) */
     float dt_min, dt_max, beta;  /* Eq. 5 parameters */
-    int32_t n_s;                 /* samples per segment N_S: 4, 8, 16 or 32 */
+    int32_t n_s;                 /* samples per segment N_S: 4, 8, 16 or 32; 0 = the scene's last
+                                    rgx_autotune pick, else 16.  N_S is part of the method in adaptive
+                                    mode (Eq. 5 scales with it), so 0 may change results after tuning */
     float t_eps;                 /* transmittance threshold T_eps (Algorithm 1) */
     float sigma_eps;             /* truncation density: support is sigma(x) >= sigma_eps */
     float bg[3];                 /* background colour, added as T_final * bg */
-    int32_t tile_w, tile_h;      /* ray tile, tile_w * tile_h == 32 (ZTILES only) */
-    int32_t hit_cap;             /* chord-list capacity per ray (multiple of 32, 32..1024); never drops hits */
-    int32_t max_segments;        /* loop bound per ray; 0 = derived from the ray length: (t_f - t_n) / dt
-                                    (uniform) or / (N_S dt_min) (Eq. 5), plus 8, at most 2e9.  A scene box
-                                    vast next to the step (say one Gaussian of enormous scale) then lets
-                                    every ray march that far: give max_segments or t_far to bound the work */
+    int32_t tile_w, tile_h;      /* ray tile, tile_w * tile_h == 32 (ZTILES only); both 0 = the scene's
+                                    last rgx_autotune pick, else 32 x 1 */
+    int32_t hit_cap;             /* chord-list capacity per ray (multiple of 32, 32..1024; never drops hits);
+                                    0 = the scene's last rgx_autotune pick, else 512 */
+    int32_t max_segments;        /* loop bound per ray, >= 0; 0 = derived from the ray length: (t_f - t_n) / dt
+                                    (uniform) or / (N_S dt_min) (Eq. 5), plus 8, but at most 2^20
+                                    (1,048,576) segments.  A ray stopped by either bound sets
+                                    RGX_ERR_ITER_LIMIT and keeps what it has composited so far */
 } rgx_opts;
+/* Tile shape, hit_cap and (in uniform mode) N_S change scheduling only: results agree to float32
+ * rounding for any choice.  Zeros are resolved on the host at each call, so a forward and its
+ * adjoint resolve them alike as long as no rgx_autotune runs on the scene in between. */
 
 /* Create / destroy a scene handle bound to CUDA device `device`. */
 rgx_status rgx_scene_create(rgx_scene** out, int32_t device);
@@ -172,23 +179,32 @@ rgx_status rgx_render_backward(rgx_scene* scene, const rgx_camera* cams, int32_t
                                float* d_means, float* d_scales, float* d_quats,
                                float* d_densities, float* d_sh, void* stream);
 
+/* rgx_autotune modes (may be OR-ed) */
+#define RGX_TUNE_NS          1   /* also tune N_S over {4, 8, 16, 32} */
+#define RGX_TUNE_EXHAUSTIVE  2   /* time the full grid instead of one knob at a time */
+
 /*
  * Autotuner for the open knobs of Algorithm 1 -- samples per segment N_S, the
  * capacity of the hit-primitive buffer H_b (hit_cap) -- and of the 2D ray
- * tiles of Sec. 3.3 (tile_w x tile_h, when RGX_ZTILES is set).  Each candidate
- * (4 tile shapes x hit_cap in {128,192,256,384,512,640,768} x N_S in {8,16,32} when
- * tune_ns != 0, else base->n_s) is run once to warm up and twice timed with
- * CUDA events on `stream`, forward only or forward + adjoint
- * (with_backward != 0), on the caller's scene and cameras; the fastest
- * options are written to *best (other fields copied from *base) and the time
- * in ms to *best_ms (may be NULL).  Synchronises the stream.  rgba,
- * fwd_state, d_rgba and the five gradient arrays are caller-owned scratch
- * buffers laid out as for rgx_render_forward / rgx_render_backward; their
- * contents are undefined afterwards.  Note that N_S changes results in
- * adaptive mode (Eq. 5 scales with N_S), so tune_ns = 0 keeps results fixed.
+ * tiles of Sec. 3.3 (tile_w x tile_h, when RGX_ZTILES is set), timed on the
+ * caller's scene and cameras.  Candidates: 4 tile shapes (8x4, 4x8, 16x2,
+ * 32x1), hit_cap in {128,192,256,384,512,640,768}, and with RGX_TUNE_NS N_S in
+ * {4,8,16,32} (else base->n_s).  By default the knobs are tuned one at a time
+ * (tile shape at the base hit_cap, then hit_cap, then N_S: at most 4+6+3
+ * candidates); RGX_TUNE_EXHAUSTIVE times every combination.  Each candidate runs
+ * once to warm up and twice timed with CUDA events on `stream`, forward only or
+ * forward + adjoint (with_backward != 0).  Knobs left at 0 in *base start from
+ * the defaults.  The fastest options are written to *best (other fields copied
+ * from *base), its time in ms to *best_ms (may be NULL), and kept on the scene:
+ * later calls that leave hit_cap, the tile shape or n_s at 0 use them.
+ * Synchronises the stream.  rgba, fwd_state, d_rgba and the five gradient
+ * arrays are caller-owned scratch buffers laid out as for rgx_render_forward /
+ * rgx_render_backward; their contents are undefined afterwards.  N_S changes
+ * results in adaptive mode (Eq. 5 scales with N_S); without RGX_TUNE_NS results
+ * stay fixed.
  */
 rgx_status rgx_autotune(rgx_scene* scene, const rgx_camera* cams, int32_t ncam, const rgx_opts* base,
-                        int32_t tune_ns, int32_t with_backward, float* rgba, void* fwd_state,
+                        int32_t mode, int32_t with_backward, float* rgba, void* fwd_state,
                         const float* d_rgba, float* d_means, float* d_scales, float* d_quats,
                         float* d_densities, float* d_sh, rgx_opts* best, float* best_ms, void* stream);
 
@@ -213,6 +229,16 @@ rgx_status rgx_isotropic_loss(int64_t n, const float* scales, float r0, float we
  */
 rgx_status rgx_densify_accumulate(int64_t n, const float* means, const float* d_means,
                                   const rgx_camera* cam, float* stat, int32_t* count, void* stream);
+
+/*
+ * Cap the forward's tape (the finished first chord lists the adjoint reads back
+ * instead of traversing again; 48 B per entry, by default hit_cap / 6 entries per
+ * ray, e.g. 29 GB for 7.1 M rays at hit_cap 512) at max_entries entries; 0
+ * disables the tape, a negative value restores the default sizing.  Results do
+ * not depend on it: rays whose lists find no room are collected again by the
+ * adjoint.  Takes effect at the next rgx_render_forward with a state.
+ */
+rgx_status rgx_set_tape_limit(rgx_scene* scene, int64_t max_entries);
 
 /* Synchronise `stream`, return the device status word (RGX_ERR_* bits, 0 if
  * clean) and clear it. */
@@ -265,6 +291,10 @@ rgx_status rgx_get_counters(rgx_scene* scene, uint64_t* out8, void* stream);
  *     streams, other threads) race and must be serialised by the caller.
  *   - means, codes and perm are device pointers on the current device;
  *     the work is enqueued on `stream`.
+ *   - Means are not checked (unlike rgx_build_bvh, which flags them in the
+ *     scene's status word): a NaN coordinate is left out of the bounds and
+ *     quantised to cell 0, an infinite one makes the extent infinite so every
+ *     code becomes 0; the call still returns RGX_OK.
  */
 rgx_status rgx_morton_sort_noalloc(int64_t n, const float* means, int32_t wide, uint64_t* codes,
                                    int32_t* perm, void* stream);

@@ -17,6 +17,7 @@
 //               grandchildren as half-precision boxes, rounded outward
 #include <stdio.h>
 #include <cuda_fp16.h>
+#include <atomic>
 #include "common.cuh"
 
 #define FULLMASK 0xffffffffu
@@ -498,7 +499,9 @@ extern "C" rgx_status rgx_build_bvh(rgx_scene* s, int64_t n, int32_t sh_degree, 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RGX_NOALLOC_BYTES];
 
 #define RGX_MAX_DEVICES 64
-static void* g_noalloc_addr[RGX_MAX_DEVICES];
+// per device: the array's device address, looked up by the first call on that device;
+// atomic, since two host threads may make that first call at the same time
+static std::atomic<void*> g_noalloc_addr[RGX_MAX_DEVICES];
 
 // per-axis min/max of the means only (no other parameter is read here)
 __global__ void k_bounds_means(int64_t n, const float* __restrict__ means, unsigned int* __restrict__ bounds) {
@@ -536,14 +539,14 @@ extern "C" rgx_status rgx_morton_sort_noalloc(int64_t n, const float* means, int
     RGX_CUDA(nullptr, cudaGetDevice(&dev));
     if (dev < 0 || dev >= RGX_MAX_DEVICES)
         return set_err(nullptr, RGX_ERR_INVALID_ARG, "rgx_morton_sort_noalloc: device index too large");
-    if (!g_noalloc_addr[dev]) {
+    void* addr = g_noalloc_addr[dev].load(std::memory_order_relaxed);
+    if (!addr) {
         // first call on this device: the host-side name of the array is not a
         // device address; ask the runtime for it (with this device current)
-        void* p = nullptr;
-        RGX_CUDA(nullptr, cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = p;
+        RGX_CUDA(nullptr, cudaGetSymbolAddress(&addr, g_noalloc_scratch));
+        g_noalloc_addr[dev].store(addr, std::memory_order_relaxed);
     }
-    unsigned char* base = (unsigned char*)g_noalloc_addr[dev];
+    unsigned char* base = (unsigned char*)addr;
     uint64_t* keys[2] = {(uint64_t*)base, (uint64_t*)base + RGX_NOALLOC_MAX_N};
     uint32_t* vals0 = (uint32_t*)(base + (size_t)RGX_NOALLOC_MAX_N * 16);
     uint32_t* vals[2] = {vals0, vals0 + RGX_NOALLOC_MAX_N};

@@ -30,6 +30,13 @@
 
 #define RGX_STACK 96          // >= depth of a radix tree over (63-bit code, 32-bit index) keys
 #define RGX_MAX_CAMS 1024
+// defaults of the tuning knobs left at 0 before a scene has been autotuned (the values
+// rgx_autotune picked on a 100k-Gaussian object view at 800x800)
+#define RGX_DEFAULT_HIT_CAP 512
+#define RGX_DEFAULT_TILE_W 32
+#define RGX_DEFAULT_TILE_H 1
+#define RGX_DEFAULT_NS 16
+#define RGX_SEGMENT_CEILING (1 << 20)  // per-ray segment bound when max_segments = 0
 #define RGX_BLOCK 32          // threads per block of the march kernels (one warp: finest shared-memory granularity)
 
 // ---------------------------------------------------------------- scene
@@ -63,8 +70,13 @@ struct rgx_scene {
     float4* spill = nullptr;       // adjoint scratch: chunk entries of overflowing segments, per resident warp
     size_t spill_cap = 0;          // in float4
     float4* tape = nullptr;        // the last forward's first-window lists: 3 planes of tape_cap float4
-    size_t tape_cap = 0;           // in entries
+    size_t tape_cap = 0;           // entries the last forward with a state could use (the planes' stride)
+    size_t tape_alloc = 0;         // entries allocated
     uint32_t tape_gen = 0, tape_tag = 0;  // tag of the forward call whose lists the tape holds
+    int64_t tape_limit = -1;       // caller's cap on tape entries (< 0: hit_cap / 6 per ray)
+    // the last rgx_autotune result: what tuning knobs left at 0 select
+    int has_tuned = 0;
+    int tuned_hit_cap = 0, tuned_tile_w = 0, tuned_tile_h = 0, tuned_n_s = 0;
     // render
     rgx_camera* cams = nullptr; int cams_cap = 0;
     unsigned int* queue = nullptr; // [4] persistent work counters

@@ -36,6 +36,9 @@
 #include <cuda_fp16.h>
 #include "common.cuh"
 
+// Version of the march kernels: changed whenever their code changes, so that
+// profiler counters taken on an older version are not attributed to this one.
+#define RGX_MARCH_VERSION "m2-1"
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
@@ -46,6 +49,7 @@
 #define CUT 32                                      // child records of a tile's BVH cut
 #define SPILL_CAP 4096                              // adjoint: chunk entries kept per warp in global scratch
 #define TAPE_CHUNK 2048                             // tape entries a warp reserves at a time
+#define TAPE_FULL 0xffffffffu                       // a warp's tape_base once a reservation has failed
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -757,13 +761,22 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 if (!BWD && P.tape_cap > 0) {
                     // tape the finished list (entries in list order) for the adjoint, in the
                     // warp's current chunk of the tape (a new chunk when it is used up)
-                    if ((uint32_t)nL > tape_left) {
+                    if ((uint32_t)nL > tape_left && tape_base != TAPE_FULL) {
+                        // A warp stops reserving once one reservation has failed, and never adds to a
+                        // counter already at the capacity: the counter then stays below
+                        // tape_cap + (resident warps) x TAPE_CHUNK < 2^32 (tape_cap < 2^31), so it
+                        // cannot wrap round and hand out a chunk that another ray's list occupies.
                         const uint32_t want = max((uint32_t)TAPE_CHUNK, (uint32_t)nL);
-                        uint32_t base = 0;
-                        if (lane == 0) base = atomicAdd(P.tape_n, want);
+                        uint32_t base = TAPE_FULL;
+                        if (lane == 0 && *(volatile uint32_t*)P.tape_n < P.tape_cap) base = atomicAdd(P.tape_n, want);
                         base = __shfl_sync(FULLMASK, base, 0);
-                        if ((uint64_t)base + want <= (uint64_t)P.tape_cap) { tape_base = base; tape_left = want; }
-                        else tape_left = 0;
+                        if (base != TAPE_FULL && (uint64_t)base + want <= (uint64_t)P.tape_cap) {
+                            tape_base = base;
+                            tape_left = want;
+                        } else {
+                            tape_base = TAPE_FULL;
+                            tape_left = 0;
+                        }
                     }
                     if ((uint32_t)nL <= tape_left) {
                         float4* tq = P.tape + tape_base;
@@ -796,7 +809,12 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         }
     }
     const float minstep = uniform ? P.dt : (float)NS * fminf(P.dt_min, P.dt_max);
-    const int iter_cap = P.max_segments > 0 ? P.max_segments : (int)fminf((tf - tn) / minstep, 2.0e9f) + 8;
+    // max_segments = 0: the ray's own bound, (t_f - t_n) / minstep + 8, but never above
+    // RGX_SEGMENT_CEILING, so that a scene box vast next to the step cannot keep a warp busy
+    // for minutes; a ray stopped there sets RGX_ERR_ITER_LIMIT like one stopped by max_segments
+    const int iter_cap = P.max_segments > 0
+        ? P.max_segments
+        : (int)fminf((tf - tn) / minstep + 8.0f, (float)RGX_SEGMENT_CEILING);
     int iters = 0;
     while (P.n > 0 && tS < tf && T > P.t_eps) {
         if (iters >= iter_cap) {
@@ -1379,10 +1397,20 @@ static void* pick_kernel(int ns, bool bwd) {
     return nullptr;
 }
 
-static rgx_status check_opts(rgx_scene* s, const rgx_opts* o) {
-    if (!o) return set_err(s, RGX_ERR_INVALID_ARG, "null opts");
+// Fills the tuning knobs left at 0 -- hit_cap, the tile shape (both 0), N_S -- with the
+// scene's last rgx_autotune result, else the defaults, then checks the options.
+static rgx_status check_opts(rgx_scene* s, const rgx_opts* in, rgx_opts* o) {
+    if (!in) return set_err(s, RGX_ERR_INVALID_ARG, "null opts");
+    *o = *in;
+    const bool tuned = s && s->has_tuned;
+    if (o->hit_cap == 0) o->hit_cap = tuned ? s->tuned_hit_cap : RGX_DEFAULT_HIT_CAP;
+    if (o->tile_w == 0 && o->tile_h == 0) {
+        o->tile_w = tuned ? s->tuned_tile_w : RGX_DEFAULT_TILE_W;
+        o->tile_h = tuned ? s->tuned_tile_h : RGX_DEFAULT_TILE_H;
+    }
+    if (o->n_s == 0) o->n_s = tuned ? s->tuned_n_s : RGX_DEFAULT_NS;
     if (o->n_s != 4 && o->n_s != 8 && o->n_s != 16 && o->n_s != 32)
-        return set_err(s, RGX_ERR_INVALID_ARG, "n_s must be 4, 8, 16 or 32");
+        return set_err(s, RGX_ERR_INVALID_ARG, "n_s must be 0, 4, 8, 16 or 32");
     if (o->flags & RGX_ADAPTIVE) {
         if (!(o->dt_min > 0.0f) || !(o->dt_max >= o->dt_min) || !(o->beta > 0.0f))
             return set_err(s, RGX_ERR_INVALID_ARG, "adaptive mode needs 0 < dt_min <= dt_max and beta > 0");
@@ -1390,10 +1418,11 @@ static rgx_status check_opts(rgx_scene* s, const rgx_opts* o) {
         return set_err(s, RGX_ERR_INVALID_ARG, "dt must be > 0");
     }
     if (o->hit_cap < 32 || o->hit_cap > 1024 || (o->hit_cap & 31))
-        return set_err(s, RGX_ERR_INVALID_ARG, "hit_cap must be a multiple of 32 in [32, 1024]");
+        return set_err(s, RGX_ERR_INVALID_ARG, "hit_cap must be 0 or a multiple of 32 in [32, 1024]");
     if ((o->flags & RGX_ZTILES) && (o->tile_w <= 0 || o->tile_h <= 0 || o->tile_w * o->tile_h != 32))
-        return set_err(s, RGX_ERR_INVALID_ARG, "tile_w * tile_h must be 32");
+        return set_err(s, RGX_ERR_INVALID_ARG, "tile_w * tile_h must be 32 (or both 0)");
     if (!(o->t_eps >= 0.0f)) return set_err(s, RGX_ERR_INVALID_ARG, "t_eps must be >= 0");
+    if (o->max_segments < 0) return set_err(s, RGX_ERR_INVALID_ARG, "max_segments must be >= 0");
     return RGX_OK;
 }
 
@@ -1422,7 +1451,7 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     P.flags = o->flags;
     P.dt = o->dt; P.dt_min = o->dt_min; P.dt_max = o->dt_max; P.beta = o->beta; P.t_eps = o->t_eps;
     P.bg0 = o->bg[0]; P.bg1 = o->bg[1]; P.bg2 = o->bg[2];
-    P.tile_w = o->tile_w > 0 ? o->tile_w : 8; P.tile_h = o->tile_h > 0 ? o->tile_h : 4;
+    P.tile_w = o->tile_w > 0 ? o->tile_w : RGX_DEFAULT_TILE_W; P.tile_h = o->tile_h > 0 ? o->tile_h : RGX_DEFAULT_TILE_H;
     P.hit_cap = o->hit_cap; P.max_segments = o->max_segments;
     P.rgba = (float4*)rgba; P.state = (float4*)state;
     P.d_rgba = (const float4*)d_rgba; P.grad = s->grad;
@@ -1486,11 +1515,14 @@ static rgx_status ensure_cams(rgx_scene* s, int ncam) {
     return RGX_OK;
 }
 
-static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* o, float* rgba,
-                                 void* state, float* sched, int32_t sched_cap, int32_t* sched_n, void* stream) {
+static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* in,
+                                 float* rgba, void* state, float* sched, int32_t sched_cap, int32_t* sched_n,
+                                 void* stream) {
     if (!s) return set_err(s, RGX_ERR_INVALID_ARG, "null scene");
     if (!s->built) return set_err(s, RGX_ERR_NOT_BUILT, "rgx_render_forward before rgx_build_bvh");
-    rgx_status r = check_opts(s, o);
+    rgx_opts ro;
+    const rgx_opts* o = &ro;
+    rgx_status r = check_opts(s, in, &ro);
     if (r) return r;
     int64_t R = 0;
     r = check_cams(s, cams, ncam, &R);
@@ -1501,17 +1533,20 @@ static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t n
     r = ensure_cams(s, ncam);
     if (r) return r;
     if (state) {
-        // room on the tape for hit_cap / 6 entries of 48 B per ray on average; a ray that
-        // finds no room is simply not taped (its adjoint collects the window itself)
-        const size_t want = (size_t)R * (size_t)(o->hit_cap / 6);
-        const size_t need = want < (size_t)0x7fffffff ? want : (size_t)0x7fffffff;
-        if (s->tape_cap < need) {
+        // room on the tape for hit_cap / 6 entries of 48 B per ray on average (or the caller's
+        // limit); a ray that finds no room is simply not taped (its adjoint collects the window
+        // itself).  tape_cap is the capacity this forward uses: the stride of the three planes.
+        size_t need = (size_t)R * (size_t)(o->hit_cap / 6);
+        if (need > (size_t)0x7fffffff) need = (size_t)0x7fffffff;
+        if (s->tape_limit >= 0 && need > (size_t)s->tape_limit) need = (size_t)s->tape_limit;
+        if (s->tape_alloc < need) {
             if (s->tape) cudaFree(s->tape);
             s->tape = nullptr;
-            s->tape_cap = 0;
-            if (cudaMalloc(&s->tape, 3 * need * sizeof(float4)) == cudaSuccess) s->tape_cap = need;
+            s->tape_alloc = 0;
+            if (cudaMalloc(&s->tape, 3 * need * sizeof(float4)) == cudaSuccess) s->tape_alloc = need;
             else { s->tape = nullptr; cudaGetLastError(); }
         }
+        s->tape_cap = s->tape_alloc < need ? s->tape_alloc : need;
     }
     return launch_march(s, cams, ncam, o, false, rgba, state, nullptr, sched, sched_cap, sched_n,
                         (cudaStream_t)stream);
@@ -1529,12 +1564,14 @@ extern "C" rgx_status rgx_render_forward_sched(rgx_scene* s, const rgx_camera* c
     return forward_common(s, cams, ncam, o, rgba, fwd_state, sched, sched_cap, sched_n, stream);
 }
 
-extern "C" rgx_status rgx_render_backward(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* o,
+extern "C" rgx_status rgx_render_backward(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* in,
                                           const void* fwd_state, const float* d_rgba, float* d_means,
                                           float* d_scales, float* d_quats, float* d_dens, float* d_sh, void* stream) {
     if (!s) return set_err(s, RGX_ERR_INVALID_ARG, "null scene");
     if (!s->built) return set_err(s, RGX_ERR_NOT_BUILT, "rgx_render_backward before rgx_build_bvh");
-    rgx_status r = check_opts(s, o);
+    rgx_opts ro;
+    const rgx_opts* o = &ro;
+    rgx_status r = check_opts(s, in, &ro);
     if (r) return r;
     int64_t R = 0;
     r = check_cams(s, cams, ncam, &R);
@@ -1563,5 +1600,11 @@ extern "C" rgx_status rgx_render_backward(rgx_scene* s, const rgx_camera* cams, 
     k_grad_finalize<<<(int)b, 256, 0, st>>>(s->n, s->morton, nk, s->grad, s->geom, s->aux, s->perm, d_means,
                                             d_scales, d_quats, d_dens, d_sh);
     RGX_CUDA(s, cudaGetLastError());
+    return RGX_OK;
+}
+
+extern "C" rgx_status rgx_set_tape_limit(rgx_scene* s, int64_t max_entries) {
+    if (!s) return set_err(s, RGX_ERR_INVALID_ARG, "rgx_set_tape_limit: null scene");
+    s->tape_limit = max_entries < 0 ? -1 : max_entries;
     return RGX_OK;
 }

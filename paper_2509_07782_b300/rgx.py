@@ -38,11 +38,12 @@ RGX_ERR_REPLAY = 64
 RGX_ERR_NOT_BUILT = 128
 
 RGX_SKIP, RGX_ADAPTIVE, RGX_MORTON, RGX_ZTILES, RGX_MORTON63 = 1, 2, 4, 8, 16
+RGX_TUNE_NS, RGX_TUNE_EXHAUSTIVE = 1, 2
 
 EXPORTS = ["rgx_scene_create", "rgx_scene_destroy", "rgx_build_bvh", "rgx_render_forward",
            "rgx_render_forward_sched", "rgx_render_backward", "rgx_sync_status", "rgx_fwd_state_bytes",
            "rgx_last_error", "rgx_get_bvh", "rgx_get_counters", "rgx_autotune",
-           "rgx_morton_sort_noalloc", "rgx_isotropic_loss", "rgx_densify_accumulate"]
+           "rgx_morton_sort_noalloc", "rgx_isotropic_loss", "rgx_densify_accumulate", "rgx_set_tape_limit"]
 
 
 class RgxCamera(C.Structure):
@@ -114,6 +115,7 @@ def lib() -> C.CDLL:
             l.rgx_morton_sort_noalloc.argtypes = [i64, fp, C.c_int32, vp, vp, vp]
             l.rgx_isotropic_loss.argtypes = [i64, fp, C.c_float, C.c_float, fp, fp, vp]
             l.rgx_densify_accumulate.argtypes = [i64, fp, fp, C.POINTER(RgxCamera), fp, vp, vp]
+            l.rgx_set_tape_limit.argtypes = [vp, i64]
             l.rgx_autotune.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), C.c_int32,
                                        C.c_int32, fp, vp, fp, fp, fp, fp, fp, fp, C.POINTER(RgxOpts),
                                        C.POINTER(C.c_float), vp]
@@ -307,9 +309,15 @@ def rgx_get_counters(h, stream=None):
     return dict(zip(keys, [int(v) for v in out]))
 
 
+def rgx_set_tape_limit(h, max_entries: int):
+    """Cap the forward's tape of first chord lists (0: no tape, < 0: default sizing)."""
+    _check(lib().rgx_set_tape_limit(h, int(max_entries)), h)
+
+
 @_traced
-def rgx_autotune(h, cams: Cameras, base, tune_ns, with_backward, rgba, state, d_rgba, grads, stream=None):
-    """Returns (best RgxOpts, best time in ms).  `grads` are scratch buffers."""
+def rgx_autotune(h, cams: Cameras, base, mode, with_backward, rgba, state, d_rgba, grads, stream=None):
+    """Returns (best RgxOpts, best time in ms).  `mode`: RGX_TUNE_NS | RGX_TUNE_EXHAUSTIVE
+    (0 = tile shape and hit_cap, one knob at a time).  `grads` are scratch buffers."""
     best = RgxOpts()
     ms = C.c_float(0.0)
     R = cams.n_rays
@@ -319,7 +327,7 @@ def rgx_autotune(h, cams: Cameras, base, tune_ns, with_backward, rgba, state, d_
     p_state = _ptr(state, "fwd_state", dtype=None, nbytes=_state_bytes(cams), optional=False)
     p_d = _ptr(d_rgba, "d_rgba", 4 * R, optional=not with_backward)
     p_g = [_ptr(x, "gradient scratch", optional=not with_backward) for x in g]
-    _check(lib().rgx_autotune(h, cams.ptr, cams.count, C.byref(base), int(tune_ns), int(with_backward),
+    _check(lib().rgx_autotune(h, cams.ptr, cams.count, C.byref(base), int(mode), int(with_backward),
                               p_rgba, p_state, p_d, *p_g, C.byref(best), C.byref(ms), _stream(stream)), h)
     return best, float(ms.value)
 
@@ -415,8 +423,10 @@ class Scene:
     def counters(self, stream=None):
         return rgx_get_counters(self.h, stream)
 
-    def autotune(self, cams: Cameras, base, tune_ns: bool = False, with_backward: bool = True, stream=None):
-        """Pick tile shape / hit_cap (/ N_S) by timing on this scene; returns (RgxOpts, ms)."""
+    def autotune(self, cams: Cameras, base, tune_ns: bool = False, with_backward: bool = True, stream=None,
+                 exhaustive: bool = False):
+        """Pick tile shape / hit_cap (/ N_S) by timing on this scene; returns (RgxOpts, ms).  The
+        scene keeps the pick: later calls whose options leave those knobs at 0 use it."""
         dev = torch.device("cuda", self.device)
         rgba = torch.empty(cams.n_rays, 4, dtype=torch.float32, device=dev)
         state = new_state(cams.n_rays, dev)
@@ -427,7 +437,11 @@ class Scene:
             grads = [torch.zeros(n, 3, device=dev), torch.zeros(n, 3, device=dev), torch.zeros(n, 4, device=dev),
                      torch.zeros(n, device=dev), torch.zeros(n, 16, 3, device=dev)]
         self._keep = cams
-        return rgx_autotune(self.h, cams, base, tune_ns, with_backward, rgba, state, d_rgba, grads, stream)
+        mode = (RGX_TUNE_NS if tune_ns else 0) | (RGX_TUNE_EXHAUSTIVE if exhaustive else 0)
+        return rgx_autotune(self.h, cams, base, mode, with_backward, rgba, state, d_rgba, grads, stream)
+
+    def set_tape_limit(self, max_entries: int):
+        rgx_set_tape_limit(self.h, max_entries)
 
 
 def scene_tensors(scene, device="cuda"):

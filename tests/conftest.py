@@ -11,3 +11,15 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300) and the built librgx")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Rounding-divergent segment decisions seen by the GPU parity comparisons."""
+    try:
+        from helpers import DIVERGENCE_LOG
+    except Exception:
+        return
+    if DIVERGENCE_LOG:
+        terminalreporter.write_sep("-", "pixels with a rounding-divergent decision (accepted by schedule replay)")
+        for name, nd, n in DIVERGENCE_LOG:
+            terminalreporter.write_line(f"{name}: {nd} of {n}")

@@ -44,23 +44,41 @@ def test_hbm_roofline_counts_the_method_bytes():
     assert g["algorithmic_bytes"] == 1000 * (236 + 32) + 64 * 16
 
 
-def test_profiled_traffic_is_keyed_on_workload_kernel_and_source_hash(monkeypatch, tmp_path):
-    import hashlib
+def test_profiled_traffic_is_keyed_on_workload_kernel_and_kernel_version(monkeypatch, tmp_path):
     src = tmp_path / "paper_2509_07782_b300" / "csrc"
     src.mkdir(parents=True)
-    (src / "march.cu").write_text("// kernel v1\n")
-    sha = hashlib.sha256(b"// kernel v1\n").hexdigest()[:16]
+    (src / "march.cu").write_text('// kernels\n#define RGX_MARCH_VERSION "v7"\n')
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "a.md").write_text(
-        f"traffic_bytes_per_launch torus_100k k_march<16,1> 123 src_sha256 {sha}\n"
-        f"traffic_bytes_per_launch outdoor_3m k_march<16,1> 456 src_sha256 {sha}\n"
-        "traffic_bytes_per_launch outdoor_3m k_march<16,0> 789 src_sha256 0000000000000000\n")
+        "traffic_bytes_per_launch torus_100k k_march<16,1> 123 kernel_version v7\n"
+        "traffic_bytes_per_launch outdoor_3m k_march<16,1> 456 kernel_version v7\n"
+        "traffic_bytes_per_launch outdoor_3m k_march<16,0> 789 kernel_version v6\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.kernel_version() == "v7"
     assert bench.profiled_traffic("k_march<16,1>", "torus_100k") == 123
     assert bench.profiled_traffic("k_march<16,1>", "outdoor_3m") == 456
     assert bench.profiled_traffic("k_march<16,1>", "plain_2k") is None
-    # counters taken on another source version do not count
+    # counters taken on another kernel version do not count
     assert bench.profiled_traffic("k_march<16,0>", "outdoor_3m") is None
+
+
+def test_the_repository_kernel_version_is_declared():
+    assert bench.kernel_version() not in ("", "unversioned")
+
+
+def test_alu_model_and_fp32_peak():
+    assert bench.alu_model(10, 2, False) == 10 * 14 + 2 * 156
+    assert bench.alu_model(10, 2, True) == 10 * 50 + 2 * 156
+    assert np.isclose(bench.fp32_peak_tflops(2032.0), 148 * 128 * 2 * 2.032e9 / 1e12)
+
+
+def test_launch_count_per_step():
+    from paper_2509_07782_b300 import rgx, synth
+    o30 = rgx.make_opts(synth.fast_options())
+    o63 = rgx.make_opts(synth.fast_options(morton63=True))
+    # build: bounds, morton, 3 per radix pass, pack, karras, refit, widen; forward march; adjoint march + finalise
+    assert bench.launches_per_step(o30) == 2 + 12 + 1 + 3 + 1 + 2
+    assert bench.launches_per_step(o63) == 2 + 24 + 1 + 3 + 1 + 2
 
 
 def test_reference_arm_prints_the_contract_line_on_the_host():

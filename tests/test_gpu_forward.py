@@ -10,15 +10,15 @@ and opacity), through the C-ABI.
   sweep 6M (64 views, one launch): seeded pixel samples at full size.
 In adaptive mode a pixel may exceed the tolerance only when the GPU took a
 segment decision that differs from the FP64 one by rounding: the oracle
-replaying the GPU's recorded schedule must then match, and such pixels must
-be rare.
+replaying the GPU's recorded schedule must then match, and there may be at
+most one such pixel per comparison (or 0.1 % of the pixels compared).
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2509_07782_b300 import synth
-from helpers import TOL_RGBA, compare_rgba, gpu_render
+from helpers import MAX_DIVERGENT_FRAC, TOL_RGBA, compare_rgba, gpu_render, record_divergence
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +41,8 @@ def test_fast_options_full_frame(res):
     o = synth.fast_options(dt=0.01)
     r = gpu_render(w.scene, [cam], o, sched_cap=64)
     assert r["status"] == 0
-    err, ndiv = compare_rgba(r["rgba"], cam, w.scene, o, gpu_sched=r["sched"], gpu_sched_n=r["sched_n"],
-                             max_divergent_frac=0.01)
+    err, ndiv = compare_rgba(r["rgba"], cam, w.scene, o, gpu_sched=r["sched"], gpu_sched_n=r["sched_n"])
+    record_divergence(f"plain_2k scene, fast options, {res[0]}x{res[1]}", ndiv, cam.n_rays)
     assert err <= TOL_RGBA
 
 
@@ -62,7 +62,8 @@ def test_torus_100k_bench_configuration_sampled():
     assert r["status"] == 0
     pix = synth.pixel_subset(cam, 4096, seed=7)
     err, ndiv = compare_rgba(r["rgba"], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"],
-                             gpu_sched_n=r["sched_n"], max_divergent_frac=0.005)
+                             gpu_sched_n=r["sched_n"])
+    record_divergence("torus_100k, bench configuration", ndiv, len(pix))
     assert err <= TOL_RGBA
     assert (r["rgba"][:, 3] > 0.5).mean() > 0.05  # the object is in view
 
@@ -75,7 +76,8 @@ def test_outdoor_3m_sampled():
     pix = synth.pixel_subset(cam, 256, seed=8)
     params = oracle.Params(w.scene)
     err, ndiv = compare_rgba(r["rgba"], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"],
-                             gpu_sched_n=r["sched_n"], max_divergent_frac=0.02, params=params)
+                             gpu_sched_n=r["sched_n"], params=params)
+    record_divergence("outdoor_3m", ndiv, len(pix))
     assert err <= TOL_RGBA
 
 
@@ -86,13 +88,18 @@ def test_batched_views_sampled(name, per_cam, ncam_checked):
     assert r["status"] == 0
     offs = np.concatenate([[0], np.cumsum([c.n_rays for c in w.cameras])])
     params = oracle.Params(w.scene)
+    ndiv_all, n_all = 0, 0
     for ci in range(0, len(w.cameras), max(1, len(w.cameras) // ncam_checked))[:ncam_checked]:
         cam = w.cameras[ci]
         pix = synth.pixel_subset(cam, per_cam, seed=100 + ci)
         sl = slice(offs[ci], offs[ci + 1])
-        err, _ = compare_rgba(r["rgba"][sl], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"][sl],
-                              gpu_sched_n=r["sched_n"][sl], max_divergent_frac=0.05, params=params)
+        err, ndiv = compare_rgba(r["rgba"][sl], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"][sl],
+                                 gpu_sched_n=r["sched_n"][sl], params=params)
         assert err <= TOL_RGBA
+        ndiv_all += ndiv
+        n_all += len(pix)
+    record_divergence(f"{name}, {ncam_checked} views", ndiv_all, n_all)
+    assert ndiv_all <= max(1, MAX_DIVERGENT_FRAC * n_all)
 
 
 @pytest.mark.parametrize("fast", [False, True])
@@ -106,8 +113,7 @@ def test_explicit_near_and_far_bounds(fast):
     o = synth.fast_options(dt=0.01) if fast else w.options
     r = gpu_render(w.scene, [cam], o, sched_cap=64)
     assert r["status"] == 0
-    err, _ = compare_rgba(r["rgba"], cam, w.scene, o, gpu_sched=r["sched"], gpu_sched_n=r["sched_n"],
-                          max_divergent_frac=0.01)
+    err, _ = compare_rgba(r["rgba"], cam, w.scene, o, gpu_sched=r["sched"], gpu_sched_n=r["sched_n"])
     assert err <= TOL_RGBA
     full = gpu_render(w.scene, w.cameras, o)
     assert np.abs(full["rgba"] - r["rgba"]).max() > 0.05  # the bounds really cut density off
