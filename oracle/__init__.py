@@ -59,13 +59,13 @@ def lib():
             l = C.CDLL(build())
             dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int64)
             l.ox_render.restype = C.c_int64
-            l.ox_render.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_int32,
+            l.ox_render.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_int32, C.c_int32, dp,
                                     C.POINTER(OxCamera), C.POINTER(OxOpts), C.c_int64, ip,
                                     dp, dp, ip, ip, C.c_int64, dp, ip, C.c_int32, C.c_int32, C.c_int32]
             l.ox_backward.restype = C.c_int64
-            l.ox_backward.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_int32,
+            l.ox_backward.argtypes = [C.c_int64, dp, dp, dp, dp, dp, C.c_int32, C.c_int32, dp,
                                       C.POINTER(OxCamera), C.POINTER(OxOpts), C.c_int64, ip, dp,
-                                      dp, dp, dp, dp, dp, C.c_int32]
+                                      dp, dp, dp, dp, dp, dp, C.c_int32]
             l.ox_sh_basis.restype = None
             l.ox_sh_basis.argtypes = [C.c_int, dp, dp]
             l.ox_quat_to_rot.restype = None
@@ -126,6 +126,10 @@ class Params:
         self.sh_degree = int(scene.sh_degree)
         nk = (self.sh_degree + 1) ** 2
         self.sh = _d(scene.sh).reshape(self.n, nk, 3)
+        sg = getattr(scene, "sg", None)
+        # spherical-Gaussian lobes: (u_x, u_y, u_z, lambda, a_r, a_g, a_b) per lobe, or none
+        self.sg = None if sg is None else _d(sg).reshape(self.n, -1, 7)
+        self.n_sg = 0 if self.sg is None else int(self.sg.shape[1])
 
     def arrays(self):
         return [self.means, self.scales, self.quats, self.dens, self.sh]
@@ -157,7 +161,7 @@ def render(scene, cam, o, pix=None, sched_cap: int = 0, sched=None, sched_n=None
         sched_n = np.zeros(npix, dtype=np.int64)
     cm, op = camera(cam), opts(o)
     nerr = lib().ox_render(P.n, _ptr(P.means), _ptr(P.scales), _ptr(P.quats), _ptr(P.dens), _ptr(P.sh),
-                           P.sh_degree, C.byref(cm), C.byref(op), npix, _ptr(pix_a),
+                           P.sh_degree, P.n_sg, _ptr(P.sg), C.byref(cm), C.byref(op), npix, _ptr(pix_a),
                            _ptr(rgba), _ptr(state), _ptr(nseg), _ptr(active),
                            int(sched_cap), _ptr(sched), _ptr(sched_n), replay, int(brute), int(nthreads))
     return dict(rgba=rgba, state=state, nseg=nseg, active=active, sched=sched, sched_n=sched_n,
@@ -171,11 +175,15 @@ def backward(scene, cam, o, d_rgba, pix=None, nthreads: int = 0, params: Params 
     npix = cam.width * cam.height if pix_a is None else int(pix_a.shape[0])
     up = _d(d_rgba).reshape(npix, 4)
     g = [np.zeros_like(a) for a in P.arrays()]
+    g_sg = np.zeros_like(P.sg) if P.sg is not None else None
     cm, op = camera(cam), opts(o)
     nerr = lib().ox_backward(P.n, _ptr(P.means), _ptr(P.scales), _ptr(P.quats), _ptr(P.dens), _ptr(P.sh),
-                             P.sh_degree, C.byref(cm), C.byref(op), npix, _ptr(pix_a), _ptr(up),
-                             *[_ptr(x) for x in g], int(nthreads))
-    return dict(means=g[0], scales=g[1], quats=g[2], densities=g[3], sh=g[4], n_iter_limit=int(nerr))
+                             P.sh_degree, P.n_sg, _ptr(P.sg), C.byref(cm), C.byref(op), npix, _ptr(pix_a), _ptr(up),
+                             *[_ptr(x) for x in g], _ptr(g_sg), int(nthreads))
+    out = dict(means=g[0], scales=g[1], quats=g[2], densities=g[3], sh=g[4], n_iter_limit=int(nerr))
+    if g_sg is not None:
+        out["sg"] = g_sg
+    return out
 
 
 def sh_basis(d, deg: int = 3) -> np.ndarray:

@@ -25,7 +25,8 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 BACKUP = os.path.join(ROOT, "oracle", "_build", "check_pins_backup")
 PINS = ["tests/test_oracle_render.py", "tests/test_oracle_grad.py", "tests/test_oracle_geometry.py",
-        "tests/test_oracle_sh.py", "tests/test_oracle_losses.py", "tests/test_oracle_morton.py"]
+        "tests/test_oracle_sh.py", "tests/test_oracle_losses.py", "tests/test_oracle_morton.py",
+        "tests/test_oracle_sg.py"]
 
 # (file, label, original text, planted text)
 MUTATIONS = [
@@ -72,8 +73,29 @@ MUTATIONS = [
      'double acc = 0.5;',
      'double acc = 0.0;'),
     ('oracle/rgx_oracle.c', 'no colour clamp',
-     'c[r] = acc > 0 ? acc : 0;',
-     'c[r] = acc;'),
+     'c[r] = pre[r] > 0 ? pre[r] : 0;',
+     'c[r] = pre[r];'),
+    ('oracle/rgx_oracle.c', 'SG lobe without -1',
+     'return exp(r[3] * (cd - 1.0));',
+     'return exp(r[3] * cd);'),
+    ('oracle/rgx_oracle.c', 'SG sharpness sign',
+     'return exp(r[3] * (cd - 1.0));',
+     'return exp(-r[3] * (cd - 1.0));'),
+    ('oracle/rgx_oracle.c', 'SG axis not normalised',
+     'double cd = (r[0]*d[0] + r[1]*d[1] + r[2]*d[2]) / nu;',
+     'double cd = (r[0]*d[0] + r[1]*d[1] + r[2]*d[2]);'),
+    ('oracle/rgx_oracle.c', 'SG amplitude channels reversed',
+     'pre[r] += p->sg[7*j + 4 + r] * e;',
+     'pre[r] += p->sg[7*j + 6 - r] * e;'),
+    ('oracle/rgx_oracle.c', 'SG axis gradient not projected',
+     'atomic_add(&gj[c], (dmu[c] - mu[c]*md) / nu);',
+     'atomic_add(&gj[c], dmu[c] / nu);'),
+    ('oracle/rgx_oracle.c', 'SG sharpness gradient without -1',
+     'atomic_add(&gj[3], sa * e * (cosv - 1.0));',
+     'atomic_add(&gj[3], sa * e * cosv);'),
+    ('oracle/rgx_oracle.c', 'SG gradient ignores the clamp',
+     'm[c] = pre[c] > 0 ? dcl[q][c] : 0.0;',
+     'm[c] = dcl[q][c];'),
     ('oracle/rgx_oracle.c', 'no lattice guard (first)',
      'int64_t jj = (int64_t)floor((th - tn) / op->dt) - 1;\n                j = jj > 0 ? jj : 0;',
      'int64_t jj = (int64_t)floor((th - tn) / op->dt);\n                j = jj > 0 ? jj : 0;'),

@@ -15,6 +15,8 @@
  *   - adaptive segment size ................ Eq. 5 (Sec. 3.2)
  *   - minimal AABB half-lengths ............ Supp. Sec. 2.2 (Cauchy-Schwarz result)
  *   - real spherical harmonics ............. Eq. 1's c_l(d) (SH appearance, Supp. Sec. 6.1)
+ *   - spherical-Gaussian lobes ............. Eq. 1's c_l(d) "with SH/SG" (Sec. 3.1); Supp.
+ *                                            Sec. 6.1 uses nine SH and seven SG per primitive
  *   - adjoint of Eq. 3 ..................... derived here; the paper trains through
  *                                            the renderer (Sec. 3.5) but prints no
  *                                            derivation.
@@ -28,8 +30,10 @@
  *   - the hit set of a segment [t_S, t_S+dS) is every Gaussian whose ellipsoid
  *     chord [t_in, t_out] overlaps it (segments lying wholly inside an ellipsoid
  *     count, Supp. Sec. 6.2);
- *   - colour activation c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_lk), d the ray
- *     direction;
+ *   - colour activation c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_lk
+ *     + sum_j a_lj exp(lambda_lj (mu_lj . d - 1))), d the ray direction; lobe j
+ *     has a raw axis normalised here (mu = u / |u|), a sharpness lambda >= 0 and
+ *     an RGB amplitude a, stored as 7 numbers (u_x, u_y, u_z, lambda, a_r, a_g, a_b);
  *   - truncation boundary, schedule and termination are piecewise constant in
  *     the adjoint (stop-gradient).
  *
@@ -90,6 +94,8 @@ typedef struct {
     double Qe;        /* 2 ln(sigma~ / sigma_eps); <= 0 means empty support */
     double K[16][3];
     int nk;
+    const double* sg; /* nsg lobes x (u_x, u_y, u_z, lambda, a_r, a_g, a_b), or NULL */
+    int nsg;
 } ox_prim;
 
 static void prim_setup(ox_prim* p, const double* mu, const double* s, const double* q,
@@ -106,6 +112,8 @@ static void prim_setup(ox_prim* p, const double* mu, const double* s, const doub
     for (int k = 0; k < 16; k++)
         for (int c = 0; c < 3; c++)
             p->K[k][c] = (k < nk) ? sh[3*k + c] : 0.0;
+    p->sg = NULL;
+    p->nsg = 0;
 }
 
 /* Half-lengths of the minimal AABB of the sigma_eps ellipsoid:
@@ -314,7 +322,7 @@ static void tape_push_contrib(ox_tape* tp, ox_contrib c)
 /* Evaluate the samples of one segment, Eq. 1 + Eq. 3.  `hits` is the hit set
  * (indices into ch).  If brute != 0 every Gaussian of the scene is evaluated at
  * every sample instead.  Colours cl[l] were computed per (ray, Gaussian). */
-static void prim_colour(const ox_prim* p, const double Y[16], double c[3], double pre[3]);
+static void prim_colour(const ox_prim* p, const double Y[16], const double d[3], double c[3], double pre[3]);
 
 static void eval_segment(const ox_prim* P, int64_t nP, const ox_chord* ch, const int64_t* hits,
                          int64_t nh, const double (*colour)[3], const int64_t* ch_of_prim,
@@ -345,7 +353,7 @@ static void eval_segment(const ox_prim* P, int64_t nP, const ox_chord* ch, const
             if (brute) {
                 /* a Gaussian without a chord can only be touched at tangency */
                 if (ch_of_prim[l] >= 0) c = colour[ch_of_prim[l]];
-                else { double pre[3]; prim_colour(p, Ybasis, ctmp, pre); c = ctmp; }
+                else { double pre[3]; prim_colour(p, Ybasis, d, ctmp, pre); c = ctmp; }
             } else {
                 c = colour[hits[h]];
             }
@@ -370,15 +378,31 @@ static void eval_segment(const ox_prim* P, int64_t nP, const ox_chord* ch, const
     }
 }
 
-/* Colour of Gaussian p seen along direction d: max(0, 1/2 + sum_k Y_k(d) K_k). */
-static void prim_colour(const ox_prim* p, const double Y[16], double c[3], double pre[3])
+/* Value exp(lambda (mu . d - 1)) of spherical-Gaussian lobe j of p along d, with
+ * mu = u / |u| its unit axis; also returns mu . d. */
+static double sg_lobe(const ox_prim* p, int j, const double d[3], double* cosv)
+{
+    const double* r = p->sg + 7*j;
+    double nu = sqrt(r[0]*r[0] + r[1]*r[1] + r[2]*r[2]);
+    double cd = (r[0]*d[0] + r[1]*d[1] + r[2]*d[2]) / nu;
+    if (cosv) *cosv = cd;
+    return exp(r[3] * (cd - 1.0));
+}
+
+/* Colour of Gaussian p seen along direction d:
+ * max(0, 1/2 + sum_k Y_k(d) K_k + sum_j a_j exp(lambda_j (mu_j . d - 1))). */
+static void prim_colour(const ox_prim* p, const double Y[16], const double d[3], double c[3], double pre[3])
 {
     for (int r = 0; r < 3; r++) {
         double acc = 0.5;
         for (int k = 0; k < p->nk; k++) acc += Y[k] * p->K[k][r];
         pre[r] = acc;
-        c[r] = acc > 0 ? acc : 0;
     }
+    for (int j = 0; j < p->nsg; j++) {
+        double e = sg_lobe(p, j, d, NULL);
+        for (int r = 0; r < 3; r++) pre[r] += p->sg[7*j + 4 + r] * e;
+    }
+    for (int r = 0; r < 3; r++) c[r] = pre[r] > 0 ? pre[r] : 0;
 }
 
 /* March one ray.  sched_in (replay) gives the evaluated segments to use
@@ -417,7 +441,7 @@ static void march_ray(const ox_prim* P, int64_t nP, int sh_deg, const ox_camera*
     double (*colour)[3] = malloc((size_t)(nch > 0 ? nch : 1) * sizeof *colour);
     for (int64_t i = 0; i < nch; i++) {
         double pre[3];
-        prim_colour(&P[ch[i].l], Y, colour[i], pre);
+        prim_colour(&P[ch[i].l], Y, d, colour[i], pre);
     }
     int64_t* hits = malloc((size_t)(nch > 0 ? nch : 1) * sizeof(int64_t));
     int64_t nrec = 0;
@@ -494,14 +518,17 @@ static void march_ray(const ox_prim* P, int64_t nP, int sh_deg, const ox_camera*
 }
 
 static ox_prim* setup_all(int64_t n, const double* means, const double* scales, const double* quats,
-                          const double* dens, const double* sh, int sh_deg, double sigma_eps)
+                          const double* dens, const double* sh, int sh_deg, int nsg, const double* sg,
+                          double sigma_eps)
 {
     int nk = (sh_deg + 1) * (sh_deg + 1);
     ox_prim* P = malloc((size_t)(n > 0 ? n : 1) * sizeof *P);
     if (!P) return NULL;
     #pragma omp parallel for schedule(static)
-    for (int64_t l = 0; l < n; l++)
+    for (int64_t l = 0; l < n; l++) {
         prim_setup(&P[l], means + 3*l, scales + 3*l, quats + 4*l, dens[l], sh + (int64_t)nk*3*l, nk, sigma_eps);
+        if (nsg > 0 && sg) { P[l].sg = sg + (int64_t)7*nsg*l; P[l].nsg = nsg; }
+    }
     return P;
 }
 
@@ -524,7 +551,7 @@ static int set_threads(int nthreads)
  * Returns the number of rays that hit the segment limit (0 when none).
  */
 int64_t ox_render(int64_t n, const double* means, const double* scales, const double* quats,
-                  const double* dens, const double* sh, int32_t sh_deg,
+                  const double* dens, const double* sh, int32_t sh_deg, int32_t n_sg, const double* sg,
                   const ox_camera* cam, const ox_opts* op,
                   int64_t npix, const int64_t* pix,
                   double* rgba, double* state, int64_t* nseg, int64_t* active,
@@ -532,7 +559,8 @@ int64_t ox_render(int64_t n, const double* means, const double* scales, const do
                   int32_t brute, int32_t nthreads)
 {
     set_threads(nthreads);
-    ox_prim* P = setup_all(n, means, scales, quats, dens, sh, sh_deg, op->sigma_eps);
+    if (n_sg < 0 || n_sg > 7 || (n_sg > 0 && !sg)) return -1;
+    ox_prim* P = setup_all(n, means, scales, quats, dens, sh, sh_deg, n_sg, sg, op->sigma_eps);
     if (!P) return -1;
     double lo[3], hi[3];
     scene_box(P, n, lo, hi);
@@ -590,15 +618,16 @@ static void atomic_add(double* a, double v)
  * with M = S^-1 R^T, chained to s, R(q^) and q.
  */
 int64_t ox_backward(int64_t n, const double* means, const double* scales, const double* quats,
-                    const double* dens, const double* sh, int32_t sh_deg,
+                    const double* dens, const double* sh, int32_t sh_deg, int32_t n_sg, const double* sg,
                     const ox_camera* cam, const ox_opts* op,
                     int64_t npix, const int64_t* pix, const double* d_rgba,
                     double* g_means, double* g_scales, double* g_quats, double* g_dens, double* g_sh,
-                    int32_t nthreads)
+                    double* g_sg, int32_t nthreads)
 {
     set_threads(nthreads);
     int nk = (sh_deg + 1) * (sh_deg + 1);
-    ox_prim* P = setup_all(n, means, scales, quats, dens, sh, sh_deg, op->sigma_eps);
+    if (n_sg < 0 || n_sg > 7 || (n_sg > 0 && (!sg || !g_sg))) return -1;
+    ox_prim* P = setup_all(n, means, scales, quats, dens, sh, sh_deg, n_sg, sg, op->sigma_eps);
     if (!P) return -1;
     double lo[3], hi[3];
     scene_box(P, n, lo, hi);
@@ -639,7 +668,7 @@ int64_t ox_backward(int64_t n, const double* means, const double* scales, const 
                 ox_contrib* cb = &tape.G[gi];
                 const ox_prim* pr = &P[cb->l];
                 double pre[3], cl[3];
-                prim_colour(pr, Y, cl, pre);
+                prim_colour(pr, Y, d, cl, pre);
                 double dg = dsig;
                 for (int c = 0; c < 3; c++) dg += dci[c] * (cl[c] - s->c[c]) / s->sigma;
                 /* dc_l accumulation (linear search is fine for an oracle) */
@@ -666,10 +695,26 @@ int64_t ox_backward(int64_t n, const double* means, const double* scales, const 
         for (int64_t q = 0; q < nid; q++) {
             const ox_prim* pr = &P[ids[q]];
             double pre[3], cl[3];
-            prim_colour(pr, Y, cl, pre);
+            prim_colour(pr, Y, d, cl, pre);
             for (int k = 0; k < nk; k++)
                 for (int c = 0; c < 3; c++)
                     if (pre[c] > 0) atomic_add(&g_sh[((int64_t)ids[q]*nk + k)*3 + c], Y[k] * dcl[q][c]);
+            /* lobe j: dc/da_c = e_j; dc_c/dlambda = a_c e_j (mu.d - 1); dc_c/dmu = a_c e_j lambda d;
+             * mu = u/|u| gives du = (dmu - mu (mu.dmu)) / |u| */
+            for (int j = 0; j < pr->nsg; j++) {
+                const double* rj = pr->sg + 7*j;
+                double cosv, e = sg_lobe(pr, j, d, &cosv);
+                double m[3], sa = 0;
+                for (int c = 0; c < 3; c++) { m[c] = pre[c] > 0 ? dcl[q][c] : 0.0; sa += m[c] * rj[4 + c]; }
+                double* gj = g_sg + ((int64_t)ids[q]*pr->nsg + j)*7;
+                for (int c = 0; c < 3; c++) atomic_add(&gj[4 + c], m[c] * e);
+                atomic_add(&gj[3], sa * e * (cosv - 1.0));
+                double nu = sqrt(rj[0]*rj[0] + rj[1]*rj[1] + rj[2]*rj[2]);
+                double mu[3] = { rj[0]/nu, rj[1]/nu, rj[2]/nu };
+                double dmu[3] = { sa*e*rj[3]*d[0], sa*e*rj[3]*d[1], sa*e*rj[3]*d[2] };
+                double md = mu[0]*dmu[0] + mu[1]*dmu[1] + mu[2]*dmu[2];
+                for (int c = 0; c < 3; c++) atomic_add(&gj[c], (dmu[c] - mu[c]*md) / nu);
+            }
         }
         free(ids); free(dcl); free(tape.S); free(tape.G);
     }

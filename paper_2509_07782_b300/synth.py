@@ -64,6 +64,7 @@ class Scene:
     densities: np.ndarray  # (N,)   float32, > 0
     sh: np.ndarray         # (N, 16, 3) float32
     sh_degree: int = 3
+    sg: np.ndarray | None = None  # (N, n_sg, 7) float32 spherical-Gaussian lobes: axis (raw), sharpness, RGB
 
     @property
     def n(self) -> int:
@@ -71,7 +72,8 @@ class Scene:
 
     def subset(self, idx) -> "Scene":
         return Scene(self.means[idx], self.scales[idx], self.quats[idx],
-                     self.densities[idx], self.sh[idx], self.sh_degree)
+                     self.densities[idx], self.sh[idx], self.sh_degree,
+                     None if self.sg is None else self.sg[idx])
 
     def permuted(self, perm) -> "Scene":
         return self.subset(np.asarray(perm))
@@ -122,6 +124,25 @@ def _finish(rng, means, log_scale_mu, log_scale_sd, log_dens_mu, log_dens_sd) ->
     dens = np.exp(rng.normal(log_dens_mu, log_dens_sd, size=n)).astype(np.float32)
     sh = rng.normal(0.0, 0.2, size=(n, SH_COEFFS, 3)).astype(np.float32)
     return Scene(means.astype(np.float32), scales, quats, dens, sh, 3)
+
+
+def with_sg_appearance(scene: Scene, seed: int, n_sg: int = 7, sh_degree: int = 2) -> Scene:
+    """The scene with the appearance model of the SH/SG comparison (Supp. Sec. 6.1):
+    SH up to ``sh_degree`` (9 coefficients per channel at degree 2) plus ``n_sg``
+    spherical-Gaussian lobes per Gaussian.  Lobe draws: axis direction uniform on the
+    sphere with a length in [0.5, 2] (the renderer normalises it), sharpness
+    log-uniform in [0.5, 30], RGB amplitude ~ N(0, 0.15)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = scene.n
+    nk = (sh_degree + 1) ** 2
+    v = rng.normal(size=(n, n_sg, 3))
+    v /= np.linalg.norm(v, axis=2, keepdims=True)
+    v *= rng.uniform(0.5, 2.0, size=(n, n_sg, 1))
+    lam = np.exp(rng.uniform(np.log(0.5), np.log(30.0), size=(n, n_sg, 1)))
+    amp = rng.normal(0.0, 0.15, size=(n, n_sg, 3))
+    sg = np.concatenate([v, lam, amp], axis=2).astype(np.float32)
+    return Scene(scene.means, scene.scales, scene.quats, scene.densities,
+                 np.ascontiguousarray(scene.sh[:, :nk, :]), sh_degree, sg)
 
 
 def cube_scene(n: int, seed: int) -> Scene:
