@@ -8,14 +8,14 @@ persistent launch) + rgx_render_backward (replayed adjoint + per-Gaussian
 finalisation).  Default workload ``batch_1m``: 1,000,000 seeded torus
 Gaussians, 8 views of uneven resolution {320x240 ... 1920x1080} (7,082,990
 rays), tile shape, hit-list capacity and N_S picked by rgx_autotune, the step
-captured in one CUDA graph.
+captured in CUDA graphs (build, forward, adjoint).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload NAME]
 
 Prints one JSON line (rank 0).  ``value`` is whole-job Mrays/s of the step
 with inputs resident in HBM, timed with CUDA events per replay on the graph's
 stream, L2 flushed (256 MiB write) between steps outside the events.  Events
-recorded inside the graph split each replay into build / forward / adjoint.
+between the build, forward and adjoint graphs split each step into stages.
 ``e2e`` repeats the step through the C-ABI with host (pinned) buffers: every
 step uploads its parameters and upstream gradient and downloads its gradients
 and image inside the timed region.  ``plain_marcher`` times the plain
@@ -51,7 +51,7 @@ WORKLOAD = "batch_1m"
 STEP_WORKLOADS = {
     "batch_1m": "1,000,000 Gaussians on a noise-perturbed torus, 8 views of uneven resolution {320x240, 640x480, "
                 "800x800, 1024x768, 1237x822, 1600x1200, 1920x1080, 512x512} on radius-4 orbits (7,082,990 rays), "
-                "BVH rebuild + one persistent forward + one persistent adjoint launch captured in a CUDA graph "
+                "BVH rebuild + one persistent forward + one persistent adjoint launch captured in CUDA graphs "
                 "(skip + adaptive Eq.5 + Z-order + Z-tiles; tile shape, hit_cap and N_S autotuned)",
     "torus_100k": "100,000 Gaussians on a noise-perturbed torus, one 800x800 view on a radius-4 orbit, BVH rebuild + "
                   "forward + adjoint (skip + adaptive Eq.5 + Z-order + Z-tiles, N_S=16)",
@@ -318,7 +318,9 @@ def _tune(args, name, sc, cams, t, opts):
                                 exhaustive=args.tune_exhaustive)
     wall = (time.perf_counter() - t0) * 1e3
     return best, {"tile": [best.tile_w, best.tile_h], "hit_cap": best.hit_cap, "n_s": best.n_s,
-                  "tuned_knobs": "tile shape, hit_cap" + (", N_S" if name in TUNE_NS else ""),
+                  "lower_first": bool(best.flags & 32),
+                  "tuned_knobs": "tile shape, hit_cap" + (", N_S" if name in TUNE_NS else "") +
+                                 ", first-window lowering",
                   "search": "exhaustive grid" if args.tune_exhaustive else "one knob at a time",
                   "best_candidate_ms": best_ms, "tuning_wall_ms": wall}
 
@@ -471,11 +473,11 @@ def run_step(args, name, rank, world, local, plain=True, e2e=True):
     upstream = torch.randn(R, 4, device=dev, generator=torch.Generator(device=dev).manual_seed(1 + rank))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts, tuned = _tune(args, name, sc, cams, t, opts)
-    step = graph.CapturedStep(sc, cams, opts, t, upstream, stage_events=True)
+    step = graph.CapturedStep(sc, cams, opts, t, upstream)
     stream = step.stream
 
-    def one():
-        step.replay()
+    def one(events=None):
+        step.replay(events)
         if world > 1:
             with torch.cuda.stream(stream):
                 rdist.allreduce_gradients(step.grad_flat, world)
@@ -495,27 +497,25 @@ def run_step(args, name, rank, world, local, plain=True, e2e=True):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-    stages = []
+    # per step: events before the build, the forward and the adjoint graphs, after the adjoint,
+    # and after the gradient all-reduce (multi-GPU)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     barrier()
     wall0 = time.perf_counter()
     for i in range(args.steps):
-        evs[i][0].record(stream)
-        one()
-        evs[i][1].record(stream)
+        one(evs[i][:4])
+        evs[i][4].record(stream)
         with torch.cuda.stream(stream):
             flush.fill_(float(i))  # L2 flush between steps, outside the events
-        stream.synchronize()   # the in-graph stage events are read after each replay
-        stages.append(step.stage_ms())
     barrier()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
-    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    step_ms = [e[0].elapsed_time(e[4]) for e in evs]
     total_ms = float(sum(step_ms))
     st = sc.status(stream)
-    build_ms = statistics.median(s[0] for s in stages)
-    fwd_ms = statistics.median(s[1] for s in stages)
-    bwd_ms = statistics.median(s[2] for s in stages)
+    build_ms = statistics.median(e[0].elapsed_time(e[1]) for e in evs)
+    fwd_ms = statistics.median(e[1].elapsed_time(e[2]) for e in evs)
+    bwd_ms = statistics.median(e[2].elapsed_time(e[3]) for e in evs)
     grads = [g.clone() for g in step.grads]
     rgba = step.rgba.clone()
 
@@ -701,7 +701,7 @@ def step_line(args, r, world):
                 "frac": achieved / fp32_peak, "traffic": traffic,
                 "peak_source": f"derived (not measured): 148 SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz; "
                                "FP32 FLOPs only, ex2 (SFU) not counted",
-                "duration": "median in-graph stage time of the launch over the timed replays (CUDA events)",
+                "duration": "median over the timed steps of its graph's replay (CUDA events on the launching stream)",
                 "work": "per (sample, listed Gaussian) pair 14 FLOPs (2x14+22 in the adjoint), per (ray, "
                         "segment, Gaussian) hit 156, from device counters"}
     hbm = hbm_roofline(r["n_touched"], r["R"], k_s, dominant_is_bwd, float(peaks.get("hbm_gbs", 6400.0)), traffic)
@@ -719,7 +719,7 @@ def step_line(args, r, world):
                    "knobs": r["tuned"]},
         "fwd_bwd_ms": r["fwd_ms"] + r["bwd_ms"], "build_ms": r["build_ms"], "fwd_ms": r["fwd_ms"],
         "bwd_ms": r["bwd_ms"], "render_mrays_s": r["R"] / r["fwd_ms"] / 1e3,
-        "stage_timing": "CUDA events recorded inside the captured graph, median over the timed replays",
+        "stage_timing": "CUDA events between the build, forward and adjoint graphs of each timed step, median",
         "plain_marcher": r["plain"],
         "speedup_vs_plain": {"render": (r["plain"]["fwd_ms"] / r["fwd_ms"]) if r["plain"] else None,
                              "fwd_bwd": (r["plain"]["fwd_bwd_ms"] / (r["fwd_ms"] + r["bwd_ms"]))

@@ -64,6 +64,9 @@ typedef int32_t rgx_status;
 #define RGX_MORTON    4    /* store packed parameters in Z-order (Sec. 3.3) */
 #define RGX_ZTILES    8    /* 2D ray tiles in Z-order instead of scanline warps (Sec. 3.3) */
 #define RGX_MORTON63  16   /* 63-bit (21 bits/axis) instead of 30-bit Morton codes */
+#define RGX_LOWER_FIRST 32 /* scheduling only (with RGX_SKIP): a ray's first chord window, tried over the whole
+                              ray, has its end lowered while its chords overflow hit_cap instead of giving up;
+                              rgx_autotune tries both, and hit_cap = 0 applies its choice */
 
 typedef struct rgx_scene rgx_scene;   /* opaque */
 
@@ -80,7 +83,7 @@ typedef struct {
 
 /* Marching options: the inputs of Algorithm 1 and Eq. 5. */
 typedef struct {
-    int32_t flags;               /* RGX_SKIP | RGX_ADAPTIVE | RGX_MORTON | RGX_ZTILES | RGX_MORTON63 */
+    int32_t flags;               /* RGX_SKIP | RGX_ADAPTIVE | RGX_MORTON | RGX_ZTILES | RGX_MORTON63 | RGX_LOWER_FIRST */
     float dt;                    /* uniform step (Eq. 3) */
     float dt_min, dt_max, beta;  /* Eq. 5 parameters */
     int32_t n_s;                 /* samples per segment N_S: 4, 8, 16 or 32; 0 = the scene's last
@@ -131,6 +134,25 @@ rgx_status rgx_build_bvh(rgx_scene* scene, int64_t n, int32_t sh_degree,
                          const rgx_opts* opts, void* stream);
 
 /*
+ * rgx_build_bvh for Gaussians whose colour also has spherical-Gaussian lobes:
+ * the SH + SG appearance of Eq. 1 ("parameterized with SH/SG", Sec. 3.1), as in
+ * the supplementary's comparison (Supp. Sec. 6.1: nine SH and seven SG per
+ * primitive, i.e. sh_degree 2 and n_sg 7).  The colour becomes
+ *     c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_lk + sum_j a_lj exp(lambda_lj (mu_lj . d - 1)))
+ *   sg   [n, n_sg, 7]  per lobe (u_x, u_y, u_z, lambda, a_r, a_g, a_b): a raw axis u
+ *                      (normalised here: mu = u / |u|, |u| > 0), a sharpness
+ *                      lambda >= 0 and an RGB amplitude; bad values are flagged
+ *                      RGX_ERR_BAD_PARAMS and the lobe is dropped
+ *   n_sg 0..7
+ * The lobes are packed in the scene (32 B per lobe per Gaussian); their gradients
+ * come from rgx_render_backward_ex.
+ */
+rgx_status rgx_build_bvh_sg(rgx_scene* scene, int64_t n, int32_t sh_degree,
+                            const float* means, const float* scales, const float* quats,
+                            const float* densities, const float* sh, int32_t n_sg, const float* sg,
+                            const rgx_opts* opts, void* stream);
+
+/*
  * Forward render of ncam cameras in one persistent launch (Algorithm 1 for
  * every pixel; Eq. 1 densities and SH colours; Eq. 3 compositing).
  *
@@ -179,6 +201,32 @@ rgx_status rgx_render_backward(rgx_scene* scene, const rgx_camera* cams, int32_t
                                float* d_means, float* d_scales, float* d_quats,
                                float* d_densities, float* d_sh, void* stream);
 
+/*
+ * rgx_render_backward with its optional outputs (any of them may be NULL):
+ *   d_sg   [n, n_sg, 7]  += gradients of the spherical-Gaussian lobes of a scene
+ *                        built by rgx_build_bvh_sg (required when it has lobes):
+ *                        (raw axis u, sharpness, RGB amplitude), caller order
+ *   stat   [n] float32   the densification statistic of Sec. 3.5, Eq. 11, for
+ *   count  [n] int32     every camera of the batch (Supp. Sec. 3 relates it to
+ *                        the projected mean gradient); both or neither.  With
+ *                        L_c = sum over camera c's pixels of <d_rgba, rgba> and
+ *                        g_c = dL_c/dmu_l, every Gaussian l with g_c != 0 gets
+ *                          stat[l]  += |mu_l - o_c| / f_c * |g_c|
+ *                          count[l] += 1
+ *                        with o_c the camera centre and f_c its focal length fx
+ *                        in pixels (> 0): each camera's own gradient, not the
+ *                        gradient of the summed loss.  Densify where stat / count
+ *                        > tau (tau = 1.5e-4 in Sec. 4.2).  Per (ray, segment,
+ *                        Gaussian) hit the adjoint adds the hit's first moment to
+ *                        a per-(Gaussian, camera) slice of scene workspace (16 B x
+ *                        n x ncam), finalised by one kernel.
+ * The five parameter gradients are those of rgx_render_backward.
+ */
+rgx_status rgx_render_backward_ex(rgx_scene* scene, const rgx_camera* cams, int32_t ncam, const rgx_opts* opts,
+                                  const void* fwd_state, const float* d_rgba, float* d_means, float* d_scales,
+                                  float* d_quats, float* d_densities, float* d_sh, float* d_sg, float* stat,
+                                  int32_t* count, void* stream);
+
 /* rgx_autotune modes (may be OR-ed) */
 #define RGX_TUNE_NS          1   /* also tune N_S over {4, 8, 16, 32} */
 #define RGX_TUNE_EXHAUSTIVE  2   /* time the full grid instead of one knob at a time */
@@ -190,8 +238,8 @@ rgx_status rgx_render_backward(rgx_scene* scene, const rgx_camera* cams, int32_t
  * caller's scene and cameras.  Candidates: 4 tile shapes (8x4, 4x8, 16x2,
  * 32x1), hit_cap in {128,192,256,384,512,640,768}, and with RGX_TUNE_NS N_S in
  * {4,8,16,32} (else base->n_s).  By default the knobs are tuned one at a time
- * (tile shape at the base hit_cap, then hit_cap, then N_S: at most 4+6+3
- * candidates); RGX_TUNE_EXHAUSTIVE times every combination.  Each candidate runs
+ * (tile shape at the base hit_cap, then hit_cap, then N_S, then RGX_LOWER_FIRST
+ * toggled: at most 4+6+3+1 candidates); RGX_TUNE_EXHAUSTIVE times every combination.  Each candidate runs
  * once to warm up and twice timed with CUDA events on `stream`, forward only or
  * forward + adjoint (with_backward != 0).  Knobs left at 0 in *base start from
  * the defaults.  The fastest options are written to *best (other fields copied
@@ -239,6 +287,70 @@ rgx_status rgx_densify_accumulate(int64_t n, const float* means, const float* d_
  * adjoint.  Takes effect at the next rgx_render_forward with a state.
  */
 rgx_status rgx_set_tape_limit(rgx_scene* scene, int64_t max_entries);
+
+/*
+ * Image loss of one training step, Sec. 3.4: per camera c of a batch,
+ *     L_c = (1 - lambda) L1 + lambda DSSIM,   DSSIM = 1 - SSIM
+ * on the composited RGB of rgba (opacity is not part of the loss), with SSIM over
+ * an 11 x 11 Gaussian window (standard deviation 1.5, C1 = 0.01^2, C2 = 0.03^2, zero
+ * padding at the image border) and both terms averaged over the view's pixels and
+ * channels.  (The paper leaves these constants to the methods it builds on; lambda
+ * = 0.2 is the usual choice.)
+ *   cams    HOST [ncam]  only width and height are read
+ *   rgba    [R,4]        rendered pixels, camera-major, row-major
+ *   target  [R,3]        target RGB
+ *   loss    [ncam]       device floats, loss[c] += L_c
+ *   d_rgba  [R,4]        written (=): dL/d rgba with L = sum_c L_c (opacity column 0),
+ *                        ready for rgx_render_backward
+ * Scratch (96 B per pixel) is scene workspace; the first call on a scene uploads the
+ * window taps (make it before any stream capture).
+ */
+rgx_status rgx_image_loss(rgx_scene* scene, const rgx_camera* cams, int32_t ncam, const float* rgba,
+                          const float* target, float lambda, float* loss, float* d_rgba, void* stream);
+
+/*
+ * One Adam step (Kingma & Ba 2015) on a parameter tensor of n floats:
+ *   g = grad (or grad * exp(param) with exp_param != 0: the optimiser's variable is
+ *       the log of the value the renderer takes, e.g. log-scales and log-densities,
+ *       and grad is the gradient with respect to that value)
+ *   m = beta1 m + (1 - beta1) g;  v = beta2 v + (1 - beta2) g^2
+ *   param -= lr (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps)
+ * and, if activated != NULL, activated = exp(param) (or param): the values the next
+ * rgx_build_bvh takes.  step >= 1.  param, m, v are updated in place.
+ */
+rgx_status rgx_adam_step(int64_t n, float* param, const float* grad, float* m, float* v, float lr, float beta1,
+                         float beta2, float eps, int32_t step, int32_t exp_param, float* activated,
+                         void* stream);
+
+/*
+ * Adaptive density control driven by the criterion of Sec. 3.5, Eq. 11 (the
+ * statistic of rgx_render_backward_ex): a Gaussian l with count[l] > 0 and
+ * stat[l] / count[l] > tau (Sec. 4.2: tau = 1.5e-4) is cloned when its largest
+ * scale is at most size_threshold, else split.  (The paper keeps the clone/split
+ * rule of the methods it builds on; the reading taken is that rule.)
+ *   action [n] int32  written: 0 keep, 1 clone, 2 split
+ *   offset [n] int32  written: first output slot of Gaussian l (exclusive scan of
+ *                     1 / 2 / 2 outputs)
+ *   n_out  HOST       number of Gaussians after the step; the call synchronises the
+ *                     stream to return it (allocate the outputs of rgx_densify_apply)
+ */
+rgx_status rgx_densify_plan(rgx_scene* scene, int64_t n, const float* stat, const int32_t* count,
+                            const float* scales, float tau, float size_threshold, int32_t* action, int32_t* offset,
+                            int64_t* n_out, void* stream);
+
+/*
+ * Apply a densification plan: every Gaussian l writes its outputs at offset[l]:
+ * kept -- itself; cloned -- itself and an identical copy; split -- two children
+ * with means mu + R(q) (s * z_k), z_k = normals[l, k, :] (standard normal draws
+ * supplied by the caller, [n, 2, 3]), scales s / 1.6, rotation, density, SH and
+ * lobes unchanged.  sh_floats / sg_floats: floats per Gaussian of sh and sg (0 for
+ * none).  out_src [n_out] (may be NULL) receives each output's source index.
+ */
+rgx_status rgx_densify_apply(int64_t n, const int32_t* action, const int32_t* offset, const float* normals,
+                             const float* means, const float* scales, const float* quats, const float* densities,
+                             const float* sh, int32_t sh_floats, const float* sg, int32_t sg_floats,
+                             float* out_means, float* out_scales, float* out_quats, float* out_densities,
+                             float* out_sh, float* out_sg, int32_t* out_src, void* stream);
 
 /* Synchronise `stream`, return the device status word (RGX_ERR_* bits, 0 if
  * clean) and clear it. */

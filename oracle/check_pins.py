@@ -26,7 +26,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 BACKUP = os.path.join(ROOT, "oracle", "_build", "check_pins_backup")
 PINS = ["tests/test_oracle_render.py", "tests/test_oracle_grad.py", "tests/test_oracle_geometry.py",
         "tests/test_oracle_sh.py", "tests/test_oracle_losses.py", "tests/test_oracle_morton.py",
-        "tests/test_oracle_sg.py"]
+        "tests/test_oracle_sg.py", "tests/test_oracle_image_loss.py"]
 
 # (file, label, original text, planted text)
 MUTATIONS = [
@@ -75,6 +75,21 @@ MUTATIONS = [
     ('oracle/rgx_oracle.c', 'no colour clamp',
      'c[r] = pre[r] > 0 ? pre[r] : 0;',
      'c[r] = pre[r];'),
+    ('oracle/losses.py', 'SSIM constants swapped',
+     'SSIM_WIN, SSIM_SIGMA, SSIM_C1, SSIM_C2 = 11, 1.5, 0.01 ** 2, 0.03 ** 2',
+     'SSIM_WIN, SSIM_SIGMA, SSIM_C1, SSIM_C2 = 11, 1.5, 0.03 ** 2, 0.01 ** 2'),
+    ('oracle/losses.py', 'SSIM window sigma 1',
+     'SSIM_WIN, SSIM_SIGMA, SSIM_C1, SSIM_C2 = 11, 1.5, 0.01 ** 2, 0.03 ** 2',
+     'SSIM_WIN, SSIM_SIGMA, SSIM_C1, SSIM_C2 = 11, 1.0, 0.01 ** 2, 0.03 ** 2'),
+    ('oracle/losses.py', 'SSIM grad drops the 2 x_p factor',
+     'dS = (_blur(a, w1) + 2.0 * x * _blur(b, w1) + y * _blur(c, w1)) / n',
+     'dS = (_blur(a, w1) + x * _blur(b, w1) + y * _blur(c, w1)) / n'),
+    ('oracle/losses.py', 'SSIM covariance sign',
+     'vx, vy, cxy = exx - mx * mx, eyy - my * my, exy - mx * my',
+     'vx, vy, cxy = exx - mx * mx, eyy - my * my, exy + mx * my'),
+    ('oracle/losses.py', 'L1 gradient sign',
+     'g = (1.0 - lam) * np.sign(x - y) / n - lam * dS',
+     'g = (1.0 - lam) * np.sign(y - x) / n - lam * dS'),
     ('oracle/rgx_oracle.c', 'SG lobe without -1',
      'return exp(r[3] * (cd - 1.0));',
      'return exp(r[3] * cd);'),

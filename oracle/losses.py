@@ -53,3 +53,64 @@ def densify_update(means, d_means, cam_origin, focal, stat, count):
     seen = gn > 0
     stat += np.where(seen, alpha * gn, 0.0)
     count += seen.astype(count.dtype)
+
+
+# ---------------------------------------------------------------------------
+# Image loss of the training step (Sec. 3.4): L = (1 - lambda) L1 + lambda DSSIM
+# (+ lambda_s L_s, above).  The paper writes the total loss without fixing the
+# image terms' constants; the readings taken here: DSSIM = 1 - SSIM, SSIM with
+# an 11 x 11 Gaussian window of standard deviation 1.5, C1 = 0.01^2,
+# C2 = 0.03^2, zero padding outside the image ("same" size), averaged over
+# pixels and channels; L1 averaged the same way; lambda = 0.2.  Both terms
+# act on the composited RGB (C + T bg); opacity is not part of the loss.
+# ---------------------------------------------------------------------------
+SSIM_WIN, SSIM_SIGMA, SSIM_C1, SSIM_C2 = 11, 1.5, 0.01 ** 2, 0.03 ** 2
+
+
+def ssim_window(size: int = SSIM_WIN, sigma: float = SSIM_SIGMA) -> np.ndarray:
+    """Normalised 1-D Gaussian taps; the 2-D window is their outer product."""
+    x = np.arange(size, dtype=np.float64) - (size - 1) / 2.0
+    g = np.exp(-x * x / (2.0 * sigma * sigma))
+    return g / g.sum()
+
+
+def _blur(img: np.ndarray, w1: np.ndarray) -> np.ndarray:
+    """Window-weighted local sum with zero padding, separable: rows then columns.
+    img [H, W, C]."""
+    H, W = img.shape[:2]
+    r = len(w1) // 2
+    pad = np.zeros((H + 2 * r, W + 2 * r) + img.shape[2:])
+    pad[r:r + H, r:r + W] = img
+    tmp = sum(w1[k] * pad[:, k:k + W] for k in range(len(w1)))
+    return sum(w1[k] * tmp[k:k + H] for k in range(len(w1)))
+
+
+def ssim_terms(x: np.ndarray, y: np.ndarray):
+    """SSIM map of images x, y [H, W, C] (FP64) and its partial derivatives with
+    respect to the local statistics of x: mean mu_x, E[x^2] and E[xy]."""
+    w1 = ssim_window()
+    mx, my = _blur(x, w1), _blur(y, w1)
+    exx, eyy, exy = _blur(x * x, w1), _blur(y * y, w1), _blur(x * y, w1)
+    vx, vy, cxy = exx - mx * mx, eyy - my * my, exy - mx * my
+    A1, A2 = 2 * mx * my + SSIM_C1, 2 * cxy + SSIM_C2
+    B1, B2 = mx * mx + my * my + SSIM_C1, vx + vy + SSIM_C2
+    S = A1 * A2 / (B1 * B2)
+    dS_dmx = S * (2 * my / A1 - 2 * my / A2 - 2 * mx / B1 + 2 * mx / B2)
+    dS_dexx = -S / B2
+    dS_dexy = 2 * S / A2
+    return S, dS_dmx, dS_dexx, dS_dexy
+
+
+def image_loss(pred: np.ndarray, target: np.ndarray, lam: float = 0.2):
+    """(L, dL/dpred) of one view: L = (1 - lam) mean|pred - target| + lam (1 - mean SSIM),
+    pred and target [H, W, 3]."""
+    x = np.asarray(pred, dtype=np.float64)
+    y = np.asarray(target, dtype=np.float64)
+    n = x.size
+    S, a, b, c = ssim_terms(x, y)
+    w1 = ssim_window()
+    # d mean(S) / dx_p = (1/n) sum_q w(q - p) [a_q + 2 x_p b_q + y_p c_q]  (w symmetric)
+    dS = (_blur(a, w1) + 2.0 * x * _blur(b, w1) + y * _blur(c, w1)) / n
+    L = (1.0 - lam) * np.abs(x - y).mean() + lam * (1.0 - S.mean())
+    g = (1.0 - lam) * np.sign(x - y) / n - lam * dS
+    return float(L), g

@@ -12,7 +12,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["api.cu", "build.cu", "march.cu", "tune.cu", "loss.cu"]
+SOURCES = ["api.cu", "build.cu", "march.cu", "tune.cu", "loss.cu", "train.cu"]
 HEADERS = ["common.cuh", os.path.join("..", "..", "include", "rgx.h")]
 LIB = os.path.join(HERE, "librgx.so")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -429,9 +429,54 @@ rgx_status rgx_internal_reserve(rgx_scene* s, int64_t n) {
     return RGX_OK;
 }
 
+// Spherical-Gaussian lobes in packed order: per lobe (u / |u|, lambda) and (a_rgb, 1 / |u|)
+// from the caller's raw (u_x, u_y, u_z, lambda, a_r, a_g, a_b).  A lobe with a non-finite
+// value, a zero axis or lambda < 0 is flagged and packed as zero.
+__global__ void k_pack_sg(int64_t n, int n_sg, int morton, const float* __restrict__ sg,
+                          const uint32_t* __restrict__ sorted_idx, float4* __restrict__ sgp,
+                          unsigned int* __restrict__ status) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t l = sorted_idx[i];
+        const int64_t p = morton ? i : (int64_t)l;
+        for (int j = 0; j < n_sg; j++) {
+            const float* r = sg + ((int64_t)l * n_sg + j) * 7;
+            const float ux = r[0], uy = r[1], uz = r[2], lam = r[3];
+            const float nu = sqrtf(ux * ux + uy * uy + uz * uz);
+            const bool ok = nu > 0.0f && isfinite(nu) && isfinite(lam) && lam >= 0.0f && isfinite(r[4]) &&
+                            isfinite(r[5]) && isfinite(r[6]);
+            if (!ok) atomicOr(status, (unsigned)RGX_ERR_BAD_PARAMS);
+            const float inv = ok ? 1.0f / nu : 0.0f;
+            sgp[2 * (p * n_sg + j) + 0] = ok ? make_float4(ux * inv, uy * inv, uz * inv, lam)
+                                             : make_float4(0.f, 0.f, 1.f, 0.f);
+            sgp[2 * (p * n_sg + j) + 1] = ok ? make_float4(r[4], r[5], r[6], inv) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+static rgx_status build_common(rgx_scene* s, int64_t n, int32_t sh_degree, const float* means,
+                               const float* scales, const float* quats, const float* densities,
+                               const float* sh, int32_t n_sg, const float* sg, const rgx_opts* opts,
+                               void* stream_);
+
 extern "C" rgx_status rgx_build_bvh(rgx_scene* s, int64_t n, int32_t sh_degree, const float* means,
                                     const float* scales, const float* quats, const float* densities,
                                     const float* sh, const rgx_opts* opts, void* stream_) {
+    return build_common(s, n, sh_degree, means, scales, quats, densities, sh, 0, nullptr, opts, stream_);
+}
+
+extern "C" rgx_status rgx_build_bvh_sg(rgx_scene* s, int64_t n, int32_t sh_degree, const float* means,
+                                       const float* scales, const float* quats, const float* densities,
+                                       const float* sh, int32_t n_sg, const float* sg, const rgx_opts* opts,
+                                       void* stream_) {
+    if (n_sg < 0 || n_sg > RGX_MAX_SG) return set_err(s, RGX_ERR_INVALID_ARG, "rgx_build_bvh_sg: n_sg not in 0..7");
+    if (n_sg > 0 && n > 0 && !sg) return set_err(s, RGX_ERR_INVALID_ARG, "rgx_build_bvh_sg: null sg");
+    return build_common(s, n, sh_degree, means, scales, quats, densities, sh, n_sg, sg, opts, stream_);
+}
+
+static rgx_status build_common(rgx_scene* s, int64_t n, int32_t sh_degree, const float* means,
+                               const float* scales, const float* quats, const float* densities,
+                               const float* sh, int32_t n_sg, const float* sg, const rgx_opts* opts,
+                               void* stream_) {
     if (!s || !opts) return set_err(s, RGX_ERR_INVALID_ARG, "rgx_build_bvh: null scene or opts");
     if (n < 0 || n >= (int64_t)0x7fffffff) return set_err(s, RGX_ERR_INVALID_ARG, "rgx_build_bvh: n out of range");
     if (sh_degree < 0 || sh_degree > 3) return set_err(s, RGX_ERR_INVALID_ARG, "rgx_build_bvh: sh_degree not in 0..3");
@@ -442,8 +487,17 @@ extern "C" rgx_status rgx_build_bvh(rgx_scene* s, int64_t n, int32_t sh_degree, 
     RGX_CUDA(s, cudaSetDevice(s->device));
     rgx_status r = rgx_internal_reserve(s, n);
     if (r != RGX_OK) return r;
+    if (n_sg > 0 && s->sgp_cap < (size_t)n * n_sg * 2) {
+        if (s->sgp) cudaFree(s->sgp);
+        s->sgp = nullptr;
+        s->sgp_cap = 0;
+        if (cudaMalloc(&s->sgp, (size_t)n * n_sg * 2 * sizeof(float4)) != cudaSuccess)
+            return set_err(s, RGX_ERR_WORKSPACE, "rgx_build_bvh_sg: lobe buffer allocation failed");
+        s->sgp_cap = (size_t)n * n_sg * 2;
+    }
     s->n = n;
     s->sh_degree = sh_degree;
+    s->n_sg = n_sg;
     s->morton = (opts->flags & RGX_MORTON) ? 1 : 0;
     s->built = 1;
     if (n == 0) {
@@ -473,6 +527,7 @@ extern "C" rgx_status rgx_build_bvh(rgx_scene* s, int64_t n, int32_t sh_degree, 
     s->sorted_buf = cur;
     k_pack<<<g, T, 0, st>>>(n, sh_degree, opts->sigma_eps, s->morton, means, scales, quats, densities, sh,
                             s->vals[cur], s->perm, s->geom, s->shc, s->aux, s->leafbox, s->status);
+    if (n_sg > 0) k_pack_sg<<<g, T, 0, st>>>(n, n_sg, s->morton, sg, s->vals[cur], s->sgp, s->status);
     if (n == 1) {
         k_single<<<1, 1, 0, st>>>(s->leafbox, s->nodes, s->root);
     } else {

@@ -30,6 +30,7 @@
 
 #define RGX_STACK 96          // >= depth of a radix tree over (63-bit code, 32-bit index) keys
 #define RGX_MAX_CAMS 1024
+#define RGX_MAX_SG 7          // spherical-Gaussian lobes per Gaussian (Supp. Sec. 6.1 uses seven)
 // defaults of the tuning knobs left at 0 before a scene has been autotuned (the values
 // rgx_autotune picked on a 100k-Gaussian object view at 800x800)
 #define RGX_DEFAULT_HIT_CAP 512
@@ -67,6 +68,18 @@ struct rgx_scene {
     float* root = nullptr;         // [8] scene box
     float4* grad = nullptr;        // [16n] backward accumulators (packed order)
     int64_t grad_cap = 0;
+    int n_sg = 0;                  // spherical-Gaussian lobes per Gaussian (0..7)
+    float4* sgp = nullptr;         // [n][n_sg][2] lobes: (unit axis, sharpness), (RGB amplitude, 1/|raw axis|)
+    size_t sgp_cap = 0;            // in float4
+    float4* gsg = nullptr;         // [n][n_sg][2] adjoint accumulators: (d unit axis, d sharpness), (d amplitude)
+    size_t gsg_cap = 0;            // in float4
+    float4* vgrad = nullptr;       // [n][ncam] per-camera V moments (densification statistic)
+    void* loss_ws = nullptr;       // image-loss scratch (24 floats per pixel, 2 doubles per view)
+    size_t loss_cap = 0;           // in bytes
+    int ssim_w_set = 0;            // SSIM window taps uploaded to this device
+    void* plan_ws = nullptr;       // densification plan: scan block sums and the total
+    size_t plan_cap = 0;           // in bytes
+    size_t vgrad_cap = 0;          // in float4
     float4* spill = nullptr;       // adjoint scratch: chunk entries of overflowing segments, per resident warp
     size_t spill_cap = 0;          // in float4
     float4* tape = nullptr;        // the last forward's first-window lists: 3 planes of tape_cap float4
@@ -76,7 +89,7 @@ struct rgx_scene {
     int64_t tape_limit = -1;       // caller's cap on tape entries (< 0: hit_cap / 6 per ray)
     // the last rgx_autotune result: what tuning knobs left at 0 select
     int has_tuned = 0;
-    int tuned_hit_cap = 0, tuned_tile_w = 0, tuned_tile_h = 0, tuned_n_s = 0;
+    int tuned_hit_cap = 0, tuned_tile_w = 0, tuned_tile_h = 0, tuned_n_s = 0, tuned_flags = 0;
     // render
     rgx_camera* cams = nullptr; int cams_cap = 0;
     unsigned int* queue = nullptr; // [4] persistent work counters

@@ -38,7 +38,7 @@
 
 // Version of the march kernels: changed whenever their code changes, so that
 // profiler counters taken on an older version are not attributed to this one.
-#define RGX_MARCH_VERSION "m2-1"
+#define RGX_MARCH_VERSION "m2-7"
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
@@ -54,6 +54,9 @@
 struct MarchParams {
     const float4* __restrict__ geom;
     const float4* __restrict__ shc;
+    const float4* __restrict__ sgp;  // spherical-Gaussian lobes (n_sg > 0)
+    int n_sg;
+    float4* gsg;                     // adjoint: lobe gradient accumulators (NULL: not requested)
     const int32_t* __restrict__ perm;
     const float4* __restrict__ nodes;
     const uint4* __restrict__ nodew;
@@ -71,6 +74,7 @@ struct MarchParams {
     float4* state;
     const float4* d_rgba;
     float4* grad;
+    float4* vgrad;  // adjoint with the densification statistic: per (packed Gaussian, camera) V moment
     float4* spill;  // adjoint: [grid][SPILL_CAP][3] chunk entries (q, c, pid) of an overflowing segment
     float4* tape;        // taped first-window lists, three planes of tape_cap entries: (t_c, a, q_min, Q_eps),
                          // (log2 sigma~, colour), (t_in, t_out, packed index bits, 0); forward writes, adjoint reads
@@ -216,8 +220,10 @@ __device__ __forceinline__ void local_frame(const float4* __restrict__ geom, int
     yc[2] = __fmaf_rn(tc, yd[2], dot3_rn(g3.x, g3.y, g3.z, ex, ey, ez));
 }
 
-// SH colour c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_k); Y in shared memory.
-__device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_t p, const float* Y, float c[3]) {
+// Colour c_l(d) = max(0, 1/2 + sum_k Y_k(d) K_k + sum_j a_j exp(lambda_j (mu_j . d - 1))):
+// SH (Y in shared memory) plus the Gaussian's spherical-Gaussian lobes, if any.
+__device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, const float4* __restrict__ sgp, int n_sg,
+                                          int64_t p, const float* Y, const Ray& ray, float c[3]) {
     const float4* s = shc + 12 * p;
     // two partial sums per channel (even / odd SH index) shorten the dependency chains
     float r = 0.5f, g = 0.5f, b = 0.5f, r2 = 0.0f, g2 = 0.0f, b2 = 0.0f;
@@ -230,6 +236,11 @@ __device__ __forceinline__ void sh_colour(const float4* __restrict__ shc, int64_
         r2 = __fmaf_rn(y.y, v0.w, r2); g2 = __fmaf_rn(y.y, v1.x, g2); b2 = __fmaf_rn(y.y, v1.y, b2);
         r = __fmaf_rn(y.z, v1.z, r); g = __fmaf_rn(y.z, v1.w, g); b = __fmaf_rn(y.z, v2.x, b);
         r2 = __fmaf_rn(y.w, v2.y, r2); g2 = __fmaf_rn(y.w, v2.z, g2); b2 = __fmaf_rn(y.w, v2.w, b2);
+    }
+    for (int j = 0; j < n_sg; j++) {
+        const float4 ax = __ldg(&sgp[2 * (p * n_sg + j)]), am = __ldg(&sgp[2 * (p * n_sg + j) + 1]);
+        const float e = expf(__fmul_rn(ax.w, __fsub_rn(dot3_rn(ax.x, ax.y, ax.z, ray.dx, ray.dy, ray.dz), 1.0f)));
+        r2 = __fmaf_rn(am.x, e, r2); g2 = __fmaf_rn(am.y, e, g2); b2 = __fmaf_rn(am.z, e, b2);
     }
     c[0] = fmaxf(__fadd_rn(r, r2), 0.0f); c[1] = fmaxf(__fadd_rn(g, g2), 0.0f); c[2] = fmaxf(__fadd_rn(b, b2), 0.0f);
 }
@@ -276,27 +287,82 @@ __device__ __forceinline__ int pop_count(int sp) {
     return min(min(sp, 32), max((STK - STK_RES - sp) / 4, 1));
 }
 
-// Collect into the list every Gaussian whose exact chord overlaps [ta, tb).
-// Each traversal step pops up to 32 4-wide nodes (one per lane; a lane tests
-// the node's four child boxes).  Leaves whose box meets the ray are queued and
-// their exact chords solved in full 32-lane rounds; SH colours are computed
-// afterwards for the kept (compacted) entries only.  Returns 0
-// when complete, 1 when the list would overflow (window mode: the caller
-// shrinks the window), 2 on a traversal-stack overflow.  In chunked mode a full
-// list is handed to `on_full(m)` and reset instead.
-__device__ __forceinline__ void colour_entries(const MarchParams& P, const WS& W, int from, int to) {
+// Colours of list entries [from, to), computed once the list is final.
+__device__ __forceinline__ void colour_entries(const MarchParams& P, const WS& W, const Ray& r, int from, int to) {
     const int lane = threadIdx.x & 31;
     for (int e = from + lane; e < to; e += 32) {
         float col[3];
-        sh_colour(P.shc, W.pid[e], W.Y, col);
+        sh_colour(P.shc, P.sgp, P.n_sg, W.pid[e], W.Y, r, col);
         W.c[e] = make_float4(W.c[e].x, col[0], col[1], col[2]);
     }
     __syncwarp();
 }
 
+// Ascending bitonic sort of one float per lane across the warp.
+__device__ __forceinline__ float warp_sort_asc(float v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const float o = __shfl_xor_sync(FULLMASK, v, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+        }
+    }
+    return v;
+}
+
+// Smaller window end for a list that overflows: about the median chord entry of
+// the list (from 32 evenly spaced entries), but above tb_floor.
+__device__ __forceinline__ float shrink_bound(const WS& W, int nL, float tb_floor) {
+    const int lane = threadIdx.x & 31;
+    const float v = warp_sort_asc(W.tio[(lane * nL) >> 5].x);
+    const float med = __shfl_sync(FULLMASK, v, 16);
+    return fmaxf(med, nextafterf(tb_floor, INFINITY));
+}
+
+// Keep, in order, the list entries whose chord starts before tb; returns their number.
+__device__ __forceinline__ int compact_below(const WS& W, int nL, float tb) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    int out = 0;
+    for (int b = 0; b < nL; b += 32) {
+        const int e = b + lane;
+        float4 q = make_float4(0.f, 0.f, 0.f, 0.f), c = q;
+        float2 io = make_float2(0.f, 0.f);
+        uint32_t pid = 0;
+        const bool k = e < nL && W.tio[e].x < tb;
+        if (k) { q = W.q[e]; c = W.c[e]; io = W.tio[e]; pid = W.pid[e]; }
+        const uint32_t bb = __ballot_sync(FULLMASK, k);
+        __syncwarp();
+        if (k) {
+            const int d = out + __popc(bb & lt);
+            W.q[d] = q; W.c[d] = c; W.tio[d] = io; W.pid[d] = pid;
+        }
+        out += __popc(bb);
+        __syncwarp();
+    }
+    return out;
+}
+
+// Collect into the list every Gaussian whose exact chord overlaps [ta, tb).
+// Each traversal step pops up to 32 4-wide nodes (one per lane; a lane tests
+// the node's four child boxes).  Leaves whose box meets the ray are queued and
+// their exact chords solved in full 32-lane rounds; SH colours are computed
+// afterwards for the kept entries only.
+//   Window mode (chunked = false): when the chords would overflow the list,
+// the window end tb is lowered -- to about the median chord entry of the list,
+// never to tb_floor or below -- the list keeps the chords that start before
+// it and the same traversal goes on against the smaller window (popped nodes
+// and queued leaves are tested against the current tb).  On return the list
+// holds exactly the chords overlapping [ta, tb) for the final tb.  Returns 0
+// when complete, 1 when even a window ending just above tb_floor overflows
+// (pass tb_floor >= tb to forbid lowering tb), 2 on a traversal-stack overflow.
+//   Chunked mode: tb stays; a full list is handed to `on_full(m)` and reset.
 template <bool BWD, class OnFull>
-__device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float ta, float tb, int cap, int& nL,
-                         bool chunked, OnFull on_full, Counters& cnt) {
+__device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float ta, float& tb, float tb_floor,
+                         int cap, int& nL, bool chunked, OnFull on_full, Counters& cnt, float min_extent = 0.0f) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
     int sp = 0, nsurv = 0, ncol = nL;  // entries [ncol, nL) still need their colour
@@ -373,15 +439,36 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
                 q = W.surv[nsurv - m + lane];
                 ch = chord_of(P.geom, q, r);
             }
-            const bool keep = h2 && ch.ok && ch.tout > ta && ch.tin < tb;
-            const uint32_t bk = __ballot_sync(FULLMASK, keep);
-            const int nk = __popc(bk);
+            bool keep = h2 && ch.ok && ch.tout > ta && ch.tin < tb;
+            uint32_t bk = __ballot_sync(FULLMASK, keep);
+            int nk = __popc(bk);
             if (nL + nk > cap) {
-                if (!chunked) return 1;
-                colour_entries(P, W, ncol, nL);
-                on_full(nL);
-                nL = 0;
-                ncol = 0;
+                if (chunked) {
+                    colour_entries(P, W, r, ncol, nL);
+                    on_full(nL);
+                    nL = 0;
+                    ncol = 0;
+                } else {
+                    // lower the window end until the list and this round fit; with min_extent > 0
+                    // the window must keep that much beyond its earliest chord entry
+                    while (nL + nk > cap) {
+                        float fl = tb_floor;
+                        if (min_extent > 0.0f) {
+                            float m = INFINITY;
+                            for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, ta));
+                            if (keep) m = fminf(m, fmaxf(ch.tin, ta));
+                            fl = fmaxf(fl, __fadd_rn(warp_min(m), min_extent));
+                        }
+                        const float tb2 = nL > 0 ? shrink_bound(W, nL, fl) : nextafterf(fl, INFINITY);
+                        if (!(tb2 < tb)) return 1;
+                        nL = compact_below(W, nL, tb2);
+                        tb = tb2;
+                        keep = keep && ch.tin < tb;
+                        bk = __ballot_sync(FULLMASK, keep);
+                        nk = __popc(bk);
+                    }
+                    ncol = min(ncol, nL);
+                }
             }
             if (keep) {
                 const int slot = nL + __popc(bk & lt);
@@ -395,7 +482,7 @@ __device__ int w_collect(const MarchParams& P, const WS& W, const Ray& r, float 
             __syncwarp();
         }
     }
-    colour_entries(P, W, ncol, nL);
+    colour_entries(P, W, r, ncol, nL);
     return 0;
 }
 
@@ -521,14 +608,15 @@ __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, floa
 // ------------------------------------------------------------------ per-segment work
 // Lane-parallel sample evaluation: lane = (sample k, group grp); the group's
 // lanes take every G-th hit.  Entry indices come from W.seg (idx) or 0..m-1.
+// Only lanes whose sample lies in the current piece of the segment (act) add.
 template <int NS>
-__device__ __forceinline__ void eval_entries(const WS& W, bool idx, int m, float tS, float dtk, float& sig,
-                                             float& S0, float& S1, float& S2) {
+__device__ __forceinline__ void eval_entries(const WS& W, bool idx, int m, float tS, float dtk, bool act,
+                                             float& sig, float& S0, float& S1, float& S2) {
     constexpr int G = 32 / NS;
     const int lane = threadIdx.x & 31;
     const int k = lane % NS, grp = lane / NS;
     const float half = __fmul_rn(0.5f, dtk);
-    const float base = __fadd_rn(tS, half);  // t of sample 0
+    if (!act) return;
     // four hits per iteration, all shared-memory loads issued before the math
     int h = grp;
     for (; h + 3 * G < m; h += 4 * G) {
@@ -565,21 +653,20 @@ __device__ __forceinline__ void eval_entries(const WS& W, bool idx, int m, float
             S2 = __fmaf_rn(g, c4.w, S2);
         }
     }
-    (void)base;
 }
 
 __device__ __forceinline__ void red_add4(float4* addr, float a, float b, float c, float d) {
     atomicAdd(addr, make_float4(a, b, c, d));
 }
 
-// Adjoint, hit-parallel, one segment: per entry (lane = entry) the sums over the
-// segment's samples of w, w u, w u^2 (w = (beta_k + gamma_k . c_l) g, u = t - t_c)
-// and of dL/dc_l, turned at once into the local-frame moments A0, V = sum w y,
-// P = sum w y y^T and the SH gradients, which are added to the Gaussian's
-// accumulator (15 float4 atomics).  Nothing is kept per entry between segments.
+// Adjoint, hit-parallel, one piece of a segment: per entry (lane = entry) the sums
+// over the piece's samples k in [ka, kb) of w, w u, w u^2 (w = (beta_k + gamma_k . c_l) g,
+// u = t - t_c) and of dL/dc_l, turned at once into the local-frame moments A0,
+// V = sum w y, P = sum w y y^T and the SH gradients, which are added to the
+// Gaussian's accumulator (15 float4 atomics).  Nothing is kept per entry between pieces.
 template <int NS>
 __device__ __forceinline__ void adjoint_flush(const MarchParams& P, const WS& W, const Ray& r, bool idx, int m,
-                                              float tS, float dtk) {
+                                              float tS, float dtk, int ka, int kb, int cam) {
     const int lane = threadIdx.x & 31;
     const float half = __fmul_rn(0.5f, dtk);
     for (int h = lane; h < m; h += 32) {
@@ -588,7 +675,7 @@ __device__ __forceinline__ void adjoint_flush(const MarchParams& P, const WS& W,
         const float u0 = __fadd_rn(__fsub_rn(tS, q4.x), half);
         float A0 = 0.f, A1 = 0.f, A2 = 0.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
 #pragma unroll 4
-        for (int k = 0; k < NS; k++) {
+        for (int k = ka; k < kb; k++) {
             const float u = __fmaf_rn((float)k, dtk, u0);
             const float q = __fmaf_rn(__fmul_rn(q4.y, u), u, q4.z);
             if (q <= q4.w) {
@@ -618,6 +705,8 @@ __device__ __forceinline__ void adjoint_flush(const MarchParams& P, const WS& W,
         red_add4(gp + 0, A0, V0, V1, V2);
         red_add4(gp + 1, Pm[0], Pm[1], Pm[2], Pm[3]);
         red_add4(gp + 2, Pm[4], Pm[5], 0.f, 0.f);
+        // this camera's share of V, for its own mean gradient M^T V (Eq. 11)
+        if (P.vgrad) red_add4(P.vgrad + (size_t)p * P.ncam + cam, V0, V1, V2, 0.f);
         // SH: dL/dK_k = Y_k dL/dc_l where the colour is not clamped
         const float m0 = c4.y > 0.f ? d0 : 0.f, m1 = c4.z > 0.f ? d1 : 0.f, m2 = c4.w > 0.f ? d2 : 0.f;
         const float* Y = W.Y;
@@ -630,6 +719,21 @@ __device__ __forceinline__ void adjoint_flush(const MarchParams& P, const WS& W,
                 v[t] = Y[k] * (ch == 0 ? m0 : (ch == 1 ? m1 : m2));
             }
             red_add4(gp + 4 + jx, v[0], v[1], v[2], v[3]);
+        }
+        if (P.gsg) {
+            // lobe j: dc/da = e_j, dc/dlambda = a e_j (mu.d - 1), dc/dmu = a e_j lambda d (unit axis;
+            // the projection onto the raw axis happens once per Gaussian)
+            for (int jl = 0; jl < P.n_sg; jl++) {
+                const float4 ax = __ldg(&P.sgp[2 * (p * P.n_sg + jl)]);
+                const float4 am = __ldg(&P.sgp[2 * (p * P.n_sg + jl) + 1]);
+                const float cosv = ax.x * r.dx + ax.y * r.dy + ax.z * r.dz;
+                const float e = expf(ax.w * (cosv - 1.0f));
+                const float sa = (m0 * am.x + m1 * am.y + m2 * am.z) * e;
+                const float sl = sa * ax.w;
+                float4* gs = P.gsg + 2 * (p * P.n_sg + jl);
+                red_add4(gs, sl * r.dx, sl * r.dy, sl * r.dz, sa * (cosv - 1.0f));
+                red_add4(gs + 1, m0 * e, m1 * e, m2 * e, 0.f);
+            }
         }
     }
     __syncwarp();
@@ -671,7 +775,7 @@ __device__ __forceinline__ float far_bound(const float4& lo, const float4& hi, c
 }
 
 template <int NS, bool BWD>
-__device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const rgx_camera& C, int px, int py,
+__device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int cam, const rgx_camera& C, int px, int py,
                           const float4& root_lo, const float4& root_hi, const float4& up, const float4& st,
                           const uint4& st2, Counters& cnt, bool& whole, uint32_t& tape_base,
                           uint32_t& tape_left, float4& o_rgba, float4& o_state, uint4& o_tape, int& o_nrec) {
@@ -710,7 +814,8 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
     int nrec = 0;
     int nL = 0;
     float w_lo = 1.0f, w_hi = 0.0f;  // current window (empty)
-    bool used_whole = false;
+    bool used_whole = false;  // the ray used a first window (recorded in the sign bit of its state)
+    float first_hi = 0.0f;    // that window's end (recorded for the adjoint's taped replay)
     bool dense = false;  // the last evaluated segment overflowed the list: go straight to chunks
     uint32_t tape_off = 0;
     int tape_cnt = -1;  // forward: where this ray's first-window list went on the tape (-1: not taped)
@@ -743,21 +848,21 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
             have = true;
             used_whole = true;
             w_lo = tn;
-            w_hi = tf;
-            float m = INFINITY;
-            for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, tn));
-            th = fminf(warp_min(m), tf);
+            w_hi = __uint_as_float(st2.w);
         } else if (BWD ? fwd_whole : whole) {
             nL = 0;
             if (lane == 0) cnt.windows++;
-            if (w_collect<BWD>(P, W, r, tn, tf, cap, nL, false, NoChunk(), cnt) == 0) {
+            // with RGX_LOWER_FIRST the window's end is lowered while its chords overflow the list, as
+            // long as it keeps one segment of the smallest size past its first chord (else the first
+            // segment is chunked anyway and a nearest-hit query is cheaper)
+            float tb = tf;
+            const float seg_min = __fmul_rn((float)NS, uniform ? P.dt : fminf(P.dt_min, P.dt_max));
+            const bool lower = (P.flags & RGX_LOWER_FIRST) != 0;  // else the whole ray or nothing
+            if (w_collect<BWD>(P, W, r, tn, tb, lower ? tn : tf, cap, nL, false, NoChunk(), cnt, lower ? seg_min : 0.0f) == 0) {
                 have = true;
                 used_whole = true;
                 w_lo = tn;
-                w_hi = tf;
-                float m = INFINITY;
-                for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, tn));
-                th = fminf(warp_min(m), tf);
+                w_hi = tb;
                 if (!BWD && P.tape_cap > 0) {
                     // tape the finished list (entries in list order) for the adjoint, in the
                     // warp's current chunk of the tape (a new chunk when it is used up)
@@ -799,7 +904,16 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 nL = 0;
             }
         }
-        if (!have) th = w_closest(P, W, r, tn, tf, cnt);
+        if (have) {
+            first_hi = w_hi;
+            float m = INFINITY;
+            for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, tn));
+            m = warp_min(m);
+            // no chord starts inside a window that had to be lowered: look beyond it
+            th = m < INFINITY ? fminf(m, tf) : (w_hi >= tf ? tf : w_closest(P, W, r, tn, tf, cnt));
+        } else {
+            th = w_closest(P, W, r, tn, tf, cnt);
+        }
         if (uniform) {
             const int jj = (int)floorf((th - tn) / P.dt) - 1;
             j = jj > 0 ? jj : 0;
@@ -849,7 +963,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 hi = fmaxf(hi, tcut);
                 nL = 0;
                 if (lane == 0) cnt.windows++;
-                const int rc = w_collect<BWD>(P, W, r, tS, hi, cap, nL, false, NoChunk(), cnt);
+                const int rc = w_collect<BWD>(P, W, r, tS, hi, hi, cap, nL, false, NoChunk(), cnt);
                 if (rc == 0) {
                     w_lo = tS; w_hi = hi;
                     wlen = (nL * 4 <= cap) ? 2.0f * len : len;
@@ -883,11 +997,11 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 }
             }
             __syncwarp();
-            if (nexact) eval_entries<NS>(W, true, nexact, tS, dtk, sig, S0, S1, S2);
+            if (nexact) eval_entries<NS>(W, true, nexact, tS, dtk, true, sig, S0, S1, S2);
         } else {
             int tot = 0;
             auto onfull = [&](int m) {
-                eval_entries<NS>(W, false, m, tS, dtk, sig, S0, S1, S2);
+                eval_entries<NS>(W, false, m, tS, dtk, true, sig, S0, S1, S2);
                 if (BWD && spill_ok) {
                     // keep the chunk for the adjoint pass (no second traversal)
                     if (tot + m <= SPILL_CAP) {
@@ -905,7 +1019,8 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                 __syncwarp();
             };
             nL = 0;
-            w_collect<BWD>(P, W, r, tS, tcut, cap, nL, true, onfull, cnt);
+            float tb_c = tcut;
+            w_collect<BWD>(P, W, r, tS, tb_c, tcut, cap, nL, true, onfull, cnt);
             if (nL) onfull(nL);
             nexact = tot;
             nL = 0;
@@ -1000,7 +1115,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
             if (lane < NS) W.bg[k] = valid ? make_float4(beta, g0, g1, g2) : make_float4(0.f, 0.f, 0.f, 0.f);
             __syncwarp();
             if (!chunked) {
-                adjoint_flush<NS>(P, W, r, true, nexact, tS, dtk);
+                adjoint_flush<NS>(P, W, r, true, nexact, tS, dtk, 0, NS, cam);
                 __syncwarp();
             } else if (spill_ok) {
                 // the segment's chunks, kept by the first pass, in the same order
@@ -1013,14 +1128,15 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
                         W.pid[e] = __float_as_uint(d[2].x);
                     }
                     __syncwarp();
-                    adjoint_flush<NS>(P, W, r, false, m, tS, dtk);
+                    adjoint_flush<NS>(P, W, r, false, m, tS, dtk, 0, NS, cam);
                 }
             } else {
                 auto onfull2 = [&](int m) {
-                    adjoint_flush<NS>(P, W, r, false, m, tS, dtk);
+                    adjoint_flush<NS>(P, W, r, false, m, tS, dtk, 0, NS, cam);
                 };
                 nL = 0;
-                w_collect<BWD>(P, W, r, tS, tcut, cap, nL, true, onfull2, cnt);
+                float tb_c2 = tcut;
+                w_collect<BWD>(P, W, r, tS, tb_c2, tcut, cap, nL, true, onfull2, cnt);
                 if (nL) onfull2(nL);
                 nL = 0;
             }
@@ -1037,7 +1153,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, const 
         o_rgba = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
         // the sign bit of T (>= 0) records the first-window path for the adjoint's replay
         o_state = make_float4(C0, C1, C2, used_whole ? -T : T);
-        o_tape = make_uint4(tape_off, (uint32_t)tape_cnt, P.tape_tag, 0u);
+        o_tape = make_uint4(tape_off, (uint32_t)tape_cnt, P.tape_tag, __float_as_uint(first_hi));
         o_nrec = nrec;
     }
 }
@@ -1294,9 +1410,9 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
                 st_l = make_float4(__shfl_sync(FULLMASK, my_st.x, l), __shfl_sync(FULLMASK, my_st.y, l),
                                    __shfl_sync(FULLMASK, my_st.z, l), __shfl_sync(FULLMASK, my_st.w, l));
                 st2_l = make_uint4(__shfl_sync(FULLMASK, my_st2.x, l), __shfl_sync(FULLMASK, my_st2.y, l),
-                                   __shfl_sync(FULLMASK, my_st2.z, l), 0u);
+                                   __shfl_sync(FULLMASK, my_st2.z, l), __shfl_sync(FULLMASK, my_st2.w, l));
             }
-            march_ray<NS, BWD>(P, W, ray, cam, px, py, root_lo, root_hi, up_l, st_l, st2_l, cnt, whole, tape_base,
+            march_ray<NS, BWD>(P, W, ray, c, cam, px, py, root_lo, root_hi, up_l, st_l, st2_l, cnt, whole, tape_base,
                                tape_left, o_rgba, o_state, o_tape, o_nrec);
             if (!BWD && lane == l) { my_rgba = o_rgba; my_state = o_state; my_tape = o_tape; my_nrec = o_nrec; }
         }
@@ -1403,7 +1519,11 @@ static rgx_status check_opts(rgx_scene* s, const rgx_opts* in, rgx_opts* o) {
     if (!in) return set_err(s, RGX_ERR_INVALID_ARG, "null opts");
     *o = *in;
     const bool tuned = s && s->has_tuned;
-    if (o->hit_cap == 0) o->hit_cap = tuned ? s->tuned_hit_cap : RGX_DEFAULT_HIT_CAP;
+    if (o->hit_cap == 0) {
+        o->hit_cap = tuned ? s->tuned_hit_cap : RGX_DEFAULT_HIT_CAP;
+        // the tuned choice of first-window lowering comes with the tuned list capacity
+        if (tuned) o->flags = (o->flags & ~RGX_LOWER_FIRST) | (s->tuned_flags & RGX_LOWER_FIRST);
+    }
     if (o->tile_w == 0 && o->tile_h == 0) {
         o->tile_w = tuned ? s->tuned_tile_w : RGX_DEFAULT_TILE_W;
         o->tile_h = tuned ? s->tuned_tile_h : RGX_DEFAULT_TILE_H;
@@ -1442,10 +1562,11 @@ static rgx_status check_cams(rgx_scene* s, const rgx_camera* cams, int32_t ncam,
 
 static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* o, bool bwd,
                                float* rgba, void* state, const float* d_rgba, float* sched, int sched_cap,
-                               int32_t* sched_n, cudaStream_t st) {
+                               int32_t* sched_n, cudaStream_t st, float4* vgrad = nullptr, float4* gsg = nullptr) {
     MarchParams P;
     memset(&P, 0, sizeof P);
-    P.geom = s->geom; P.shc = s->shc; P.perm = s->perm; P.nodes = s->nodes; P.nodew = s->nodew; P.root = s->root;
+    P.geom = s->geom; P.shc = s->shc; P.perm = s->perm;
+    P.sgp = s->sgp; P.n_sg = s->n_sg; P.nodes = s->nodes; P.nodew = s->nodew; P.root = s->root;
     P.n = s->n; P.morton = s->morton;
     P.cams = s->cams; P.ncam = ncam;
     P.flags = o->flags;
@@ -1454,7 +1575,7 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     P.tile_w = o->tile_w > 0 ? o->tile_w : RGX_DEFAULT_TILE_W; P.tile_h = o->tile_h > 0 ? o->tile_h : RGX_DEFAULT_TILE_H;
     P.hit_cap = o->hit_cap; P.max_segments = o->max_segments;
     P.rgba = (float4*)rgba; P.state = (float4*)state;
-    P.d_rgba = (const float4*)d_rgba; P.grad = s->grad;
+    P.d_rgba = (const float4*)d_rgba; P.grad = s->grad; P.vgrad = vgrad; P.gsg = gsg;
     P.sched = (float2*)sched; P.sched_cap = sched_cap; P.sched_n = sched_n;
     P.queue = s->queue; P.status = s->status; P.counters = s->counters;
     P.min_items = 16u * (uint32_t)s->num_sms;
@@ -1564,9 +1685,63 @@ extern "C" rgx_status rgx_render_forward_sched(rgx_scene* s, const rgx_camera* c
     return forward_common(s, cams, ncam, o, rgba, fwd_state, sched, sched_cap, sched_n, stream);
 }
 
-extern "C" rgx_status rgx_render_backward(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* in,
-                                          const void* fwd_state, const float* d_rgba, float* d_means,
-                                          float* d_scales, float* d_quats, float* d_dens, float* d_sh, void* stream) {
+// Eq. 11 for every camera of a batched adjoint: camera c's own mean gradient of Gaussian
+// (packed index) p is M^T V_c, V_c the first moment the camera's rays added; a Gaussian
+// with a non-zero one adds |mu - o_c| / f_c |M^T V_c| to its statistic and 1 to its count.
+__global__ void k_densify_views(int64_t n, int morton, int ncam, const float4* __restrict__ vgrad,
+                                const float4* __restrict__ geom, const int32_t* __restrict__ perm,
+                                const rgx_camera* __restrict__ cams, float* stat, int32_t* count) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = morton ? (int64_t)perm[p] : p;
+        const float4 g0 = geom[4 * p], g1 = geom[4 * p + 1], g2 = geom[4 * p + 2], g3 = geom[4 * p + 3];
+        float acc = 0.0f;
+        int cnt = 0;
+        for (int c = 0; c < ncam; c++) {
+            const float4 v = vgrad[(size_t)p * ncam + c];
+            const float dx = g1.x * v.x + g2.x * v.y + g3.x * v.z;
+            const float dy = g1.y * v.x + g2.y * v.y + g3.y * v.z;
+            const float dz = g1.z * v.x + g2.z * v.y + g3.z * v.z;
+            const float gn = sqrtf(dx * dx + dy * dy + dz * dz);
+            if (gn > 0.0f) {
+                const rgx_camera& C = cams[c];
+                const float ex = g0.x - C.c2w[3], ey = g0.y - C.c2w[7], ez = g0.z - C.c2w[11];
+                acc += sqrtf(ex * ex + ey * ey + ez * ez) / C.fx * gn;
+                cnt++;
+            }
+        }
+        if (cnt) {
+            stat[l] += acc;
+            count[l] += cnt;
+        }
+    }
+}
+
+// Lobe gradients in the caller's order: the unit-axis gradient projected onto the raw axis
+// u (mu = u / |u|: du = (dmu - mu (mu . dmu)) / |u|), sharpness and amplitude as accumulated.
+__global__ void k_grad_finalize_sg(int64_t n, int n_sg, int morton, const float4* __restrict__ gsg,
+                                   const float4* __restrict__ sgp, const int32_t* __restrict__ perm, float* d_sg) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = morton ? (int64_t)perm[p] : p;
+        for (int j = 0; j < n_sg; j++) {
+            const float4 g0 = gsg[2 * (p * n_sg + j)], g1 = gsg[2 * (p * n_sg + j) + 1];
+            const float4 ax = sgp[2 * (p * n_sg + j)], am = sgp[2 * (p * n_sg + j) + 1];
+            const float md = ax.x * g0.x + ax.y * g0.y + ax.z * g0.z;
+            float* o = d_sg + (l * n_sg + j) * 7;
+            o[0] += (g0.x - ax.x * md) * am.w;
+            o[1] += (g0.y - ax.y * md) * am.w;
+            o[2] += (g0.z - ax.z * md) * am.w;
+            o[3] += g0.w;
+            o[4] += g1.x;
+            o[5] += g1.y;
+            o[6] += g1.z;
+        }
+    }
+}
+
+static rgx_status backward_common(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* in,
+                                  const void* fwd_state, const float* d_rgba, float* d_means, float* d_scales,
+                                  float* d_quats, float* d_dens, float* d_sh, float* d_sg, float* dstat,
+                                  int32_t* dcount, void* stream) {
     if (!s) return set_err(s, RGX_ERR_INVALID_ARG, "null scene");
     if (!s->built) return set_err(s, RGX_ERR_NOT_BUILT, "rgx_render_backward before rgx_build_bvh");
     rgx_opts ro;
@@ -1579,6 +1754,12 @@ extern "C" rgx_status rgx_render_backward(rgx_scene* s, const rgx_camera* cams, 
     if (!fwd_state || !d_rgba) return set_err(s, RGX_ERR_INVALID_ARG, "null fwd_state or d_rgba");
     if (s->n > 0 && (!d_means || !d_scales || !d_quats || !d_dens || !d_sh))
         return set_err(s, RGX_ERR_INVALID_ARG, "null gradient array");
+    const bool densify = dstat != nullptr || dcount != nullptr;
+    if (densify && (!dstat || !dcount)) return set_err(s, RGX_ERR_INVALID_ARG, "densification needs stat and count");
+    if (densify) {
+        for (int i = 0; i < ncam; i++)
+            if (!(cams[i].fx > 0.0f)) return set_err(s, RGX_ERR_INVALID_ARG, "densification needs fx > 0");
+    }
     cudaStream_t st = (cudaStream_t)stream;
     RGX_CUDA(s, cudaSetDevice(s->device));
     r = ensure_cams(s, ncam);
@@ -1591,8 +1772,36 @@ extern "C" rgx_status rgx_render_backward(rgx_scene* s, const rgx_camera* cams, 
             return set_err(s, RGX_ERR_WORKSPACE, "gradient accumulator allocation failed");
         s->grad_cap = s->cap_n;
     }
+    float4* vgrad = nullptr;
+    if (densify) {
+        const size_t need = (size_t)s->n * (size_t)ncam;
+        if (s->vgrad_cap < need) {
+            if (s->vgrad) cudaFree(s->vgrad);
+            s->vgrad = nullptr;
+            s->vgrad_cap = 0;
+            if (cudaMalloc(&s->vgrad, need * sizeof(float4)) != cudaSuccess)
+                return set_err(s, RGX_ERR_WORKSPACE, "per-camera moment allocation failed");
+            s->vgrad_cap = need;
+        }
+        vgrad = s->vgrad;
+        RGX_CUDA(s, cudaMemsetAsync(vgrad, 0, need * sizeof(float4), st));
+    }
+    float4* gsg = nullptr;
+    if (d_sg && s->n_sg > 0) {
+        const size_t need = (size_t)s->n * s->n_sg * 2;
+        if (s->gsg_cap < need) {
+            if (s->gsg) cudaFree(s->gsg);
+            s->gsg = nullptr;
+            s->gsg_cap = 0;
+            if (cudaMalloc(&s->gsg, need * sizeof(float4)) != cudaSuccess)
+                return set_err(s, RGX_ERR_WORKSPACE, "lobe gradient allocation failed");
+            s->gsg_cap = need;
+        }
+        gsg = s->gsg;
+        RGX_CUDA(s, cudaMemsetAsync(gsg, 0, need * sizeof(float4), st));
+    }
     RGX_CUDA(s, cudaMemsetAsync(s->grad, 0, (size_t)16 * sizeof(float4) * s->n, st));
-    r = launch_march(s, cams, ncam, o, true, nullptr, (void*)fwd_state, d_rgba, nullptr, 0, nullptr, st);
+    r = launch_march(s, cams, ncam, o, true, nullptr, (void*)fwd_state, d_rgba, nullptr, 0, nullptr, st, vgrad, gsg);
     if (r) return r;
     const int nk = (s->sh_degree + 1) * (s->sh_degree + 1);
     int64_t b = (s->n + 255) / 256;
@@ -1600,7 +1809,33 @@ extern "C" rgx_status rgx_render_backward(rgx_scene* s, const rgx_camera* cams, 
     k_grad_finalize<<<(int)b, 256, 0, st>>>(s->n, s->morton, nk, s->grad, s->geom, s->aux, s->perm, d_means,
                                             d_scales, d_quats, d_dens, d_sh);
     RGX_CUDA(s, cudaGetLastError());
+    if (gsg) {
+        k_grad_finalize_sg<<<(int)b, 256, 0, st>>>(s->n, s->n_sg, s->morton, gsg, s->sgp, s->perm, d_sg);
+        RGX_CUDA(s, cudaGetLastError());
+    }
+    if (densify) {
+        k_densify_views<<<(int)b, 256, 0, st>>>(s->n, s->morton, ncam, vgrad, s->geom, s->perm, s->cams, dstat,
+                                                dcount);
+        RGX_CUDA(s, cudaGetLastError());
+    }
     return RGX_OK;
+}
+
+extern "C" rgx_status rgx_render_backward(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* o,
+                                          const void* fwd_state, const float* d_rgba, float* d_means,
+                                          float* d_scales, float* d_quats, float* d_dens, float* d_sh, void* stream) {
+    return backward_common(s, cams, ncam, o, fwd_state, d_rgba, d_means, d_scales, d_quats, d_dens, d_sh, nullptr,
+                           nullptr, nullptr, stream);
+}
+
+extern "C" rgx_status rgx_render_backward_ex(rgx_scene* s, const rgx_camera* cams, int32_t ncam, const rgx_opts* o,
+                                             const void* fwd_state, const float* d_rgba, float* d_means,
+                                             float* d_scales, float* d_quats, float* d_dens, float* d_sh,
+                                             float* d_sg, float* stat, int32_t* count, void* stream) {
+    if (s && s->n_sg > 0 && s->n > 0 && !d_sg)
+        return set_err(s, RGX_ERR_INVALID_ARG, "rgx_render_backward_ex: the scene has lobes: d_sg is required");
+    return backward_common(s, cams, ncam, o, fwd_state, d_rgba, d_means, d_scales, d_quats, d_dens, d_sh, d_sg,
+                           stat, count, stream);
 }
 
 extern "C" rgx_status rgx_set_tape_limit(rgx_scene* s, int64_t max_entries) {

@@ -76,16 +76,19 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
         if (!r && ms < best_t) { best_t = ms; bo = o; }
     };
     if (mode & RGX_TUNE_EXHAUSTIVE) {
-        // every (tile shape, hit_cap[, N_S]) combination
+        // every (tile shape, hit_cap[, N_S], first-window lowering) combination
+        const int nlow = (base->flags & RGX_SKIP) ? 2 : 1;
         for (int ti = 0; ti < ntiles; ti++)
             for (int ci = 0; ci < 7; ci++)
-                for (int ni = 0; ni < (tune_ns ? 4 : 1); ni++) {
-                    rgx_opts o = b0;
-                    if (ntiles > 1) { o.tile_w = tiles[ti][0]; o.tile_h = tiles[ti][1]; }
-                    o.hit_cap = caps[ci];
-                    if (tune_ns) o.n_s = nss[ni];
-                    consider(o);
-                }
+                for (int ni = 0; ni < (tune_ns ? 4 : 1); ni++)
+                    for (int li = 0; li < nlow; li++) {
+                        rgx_opts o = b0;
+                        if (ntiles > 1) { o.tile_w = tiles[ti][0]; o.tile_h = tiles[ti][1]; }
+                        o.hit_cap = caps[ci];
+                        if (tune_ns) o.n_s = nss[ni];
+                        if (li) o.flags ^= RGX_LOWER_FIRST;
+                        consider(o);
+                    }
     } else {
         // coordinate descent: the tile shape at the base hit_cap and N_S, then hit_cap at the best
         // shape, then N_S at the best shape and hit_cap (each configuration timed once)
@@ -110,6 +113,12 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
                 consider(o);
             }
         }
+        if (base->flags & RGX_SKIP) {
+            // the first window lowered while it overflows, or the whole ray or nothing
+            rgx_opts o = bo;
+            o.flags ^= RGX_LOWER_FIRST;
+            consider(o);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -124,5 +133,6 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
     s->tuned_tile_w = bo.tile_w;
     s->tuned_tile_h = bo.tile_h;
     s->tuned_n_s = bo.n_s;
+    s->tuned_flags = bo.flags;
     return RGX_OK;
 }

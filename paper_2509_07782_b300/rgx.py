@@ -37,13 +37,15 @@ RGX_ERR_BAD_PARAMS = 32
 RGX_ERR_REPLAY = 64
 RGX_ERR_NOT_BUILT = 128
 
-RGX_SKIP, RGX_ADAPTIVE, RGX_MORTON, RGX_ZTILES, RGX_MORTON63 = 1, 2, 4, 8, 16
+RGX_SKIP, RGX_ADAPTIVE, RGX_MORTON, RGX_ZTILES, RGX_MORTON63, RGX_LOWER_FIRST = 1, 2, 4, 8, 16, 32
 RGX_TUNE_NS, RGX_TUNE_EXHAUSTIVE = 1, 2
 
 EXPORTS = ["rgx_scene_create", "rgx_scene_destroy", "rgx_build_bvh", "rgx_render_forward",
            "rgx_render_forward_sched", "rgx_render_backward", "rgx_sync_status", "rgx_fwd_state_bytes",
            "rgx_last_error", "rgx_get_bvh", "rgx_get_counters", "rgx_autotune",
-           "rgx_morton_sort_noalloc", "rgx_isotropic_loss", "rgx_densify_accumulate", "rgx_set_tape_limit"]
+           "rgx_morton_sort_noalloc", "rgx_isotropic_loss", "rgx_densify_accumulate", "rgx_set_tape_limit",
+           "rgx_render_backward_ex", "rgx_build_bvh_sg", "rgx_image_loss", "rgx_adam_step", "rgx_densify_plan",
+           "rgx_densify_apply"]
 
 
 class RgxCamera(C.Structure):
@@ -105,6 +107,10 @@ def lib() -> C.CDLL:
                                                    fp, C.c_int32, vp, vp]
             l.rgx_render_backward.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), vp, fp,
                                               fp, fp, fp, fp, fp, vp]
+            l.rgx_render_backward_ex.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), vp,
+                                                 fp, fp, fp, fp, fp, fp, fp, fp, vp, vp]
+            l.rgx_build_bvh_sg.argtypes = [vp, i64, C.c_int32, fp, fp, fp, fp, fp, C.c_int32, fp,
+                                           C.POINTER(RgxOpts), vp]
             l.rgx_sync_status.argtypes = [vp, vp]
             l.rgx_fwd_state_bytes.restype = C.c_size_t
             l.rgx_fwd_state_bytes.argtypes = []
@@ -116,6 +122,13 @@ def lib() -> C.CDLL:
             l.rgx_isotropic_loss.argtypes = [i64, fp, C.c_float, C.c_float, fp, fp, vp]
             l.rgx_densify_accumulate.argtypes = [i64, fp, fp, C.POINTER(RgxCamera), fp, vp, vp]
             l.rgx_set_tape_limit.argtypes = [vp, i64]
+            l.rgx_image_loss.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, fp, fp, C.c_float, fp, fp, vp]
+            l.rgx_adam_step.argtypes = [i64, fp, fp, fp, fp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32,
+                                        C.c_int32, fp, vp]
+            l.rgx_densify_plan.argtypes = [vp, i64, fp, vp, fp, C.c_float, C.c_float, vp, vp,
+                                           C.POINTER(C.c_int64), vp]
+            l.rgx_densify_apply.argtypes = [i64, vp, vp, fp, fp, fp, fp, fp, fp, C.c_int32, fp, C.c_int32,
+                                            fp, fp, fp, fp, fp, fp, vp, vp]
             l.rgx_autotune.argtypes = [vp, C.POINTER(RgxCamera), C.c_int32, C.POINTER(RgxOpts), C.c_int32,
                                        C.c_int32, fp, vp, fp, fp, fp, fp, fp, fp, C.POINTER(RgxOpts),
                                        C.POINTER(C.c_float), vp]
@@ -172,7 +185,7 @@ def make_opts(o) -> RgxOpts:
     x = RgxOpts()
     x.flags = ((RGX_SKIP if o.skip else 0) | (RGX_ADAPTIVE if o.adaptive else 0) |
                (RGX_MORTON if o.morton else 0) | (RGX_ZTILES if o.ztiles else 0) |
-               (RGX_MORTON63 if o.morton63 else 0))
+               (RGX_MORTON63 if o.morton63 else 0) | (RGX_LOWER_FIRST if getattr(o, "lower_first", False) else 0))
     x.dt, x.dt_min, x.dt_max, x.beta = o.dt, o.dt_min, o.dt_max, o.beta
     x.n_s, x.t_eps, x.sigma_eps = int(o.n_s), o.t_eps, o.sigma_eps
     for i in range(3):
@@ -278,6 +291,94 @@ def rgx_render_backward(h, cams: Cameras, opts, state, d_rgba, d_means, d_scales
     _check(lib().rgx_render_backward(h, cams.ptr, cams.count, C.byref(opts), p_state, p_d, *g, _stream(stream)), h)
 
 
+@_traced
+def rgx_render_backward_ex(h, cams: Cameras, opts, state, d_rgba, d_means, d_scales, d_quats, d_densities, d_sh,
+                           d_sg=None, stat=None, count=None, stream=None, n=None, sh_degree: int = 3, n_sg: int = 0):
+    """rgx_render_backward with the optional lobe gradients d_sg [n, n_sg, 7] and each
+    camera's Eq. 11 statistic: stat [n] float32 and count [n] int32 (both or neither)."""
+    R = cams.n_rays
+    nn = int(n) if n is not None else 0
+    _same_device(state, d_rgba, d_means, d_scales, d_quats, d_densities, d_sh, d_sg, stat, count)
+    if (stat is None) != (count is None):
+        raise ValueError("stat and count go together")
+    p_state = _ptr(state, "fwd_state", dtype=None, nbytes=_state_bytes(cams), optional=False)
+    p_d = _ptr(d_rgba, "d_rgba", 4 * R, optional=False)
+    g = _param_ptrs(nn, sh_degree, d_means, d_scales, d_quats, d_densities, d_sh, prefix="d_")
+    p_g = _ptr(d_sg, "d_sg", nn * int(n_sg) * 7)
+    p_s = _ptr(stat, "stat", nn)
+    p_c = _ptr(count, "count", nn, dtype=torch.int32)
+    _check(lib().rgx_render_backward_ex(h, cams.ptr, cams.count, C.byref(opts), p_state, p_d, *g, p_g, p_s, p_c,
+                                        _stream(stream)), h)
+
+
+@_traced
+def rgx_build_bvh_sg(h, means, scales, quats, densities, sh, sh_degree, sg, opts, stream=None):
+    """rgx_build_bvh with spherical-Gaussian lobes sg [n, n_sg, 7] (float32)."""
+    n = int(means.shape[0])
+    ptrs = _param_ptrs(n, sh_degree, means, scales, quats, densities, sh)
+    if sg.dim() != 3 or sg.shape[0] != n or sg.shape[2] != 7 or not 0 <= sg.shape[1] <= 7:
+        raise ValueError("sg must be [n, n_sg <= 7, 7]")
+    _same_device(means, sg)
+    n_sg = int(sg.shape[1])
+    p_sg = _ptr(sg, "sg", n * n_sg * 7, optional=n == 0)
+    _check(lib().rgx_build_bvh_sg(h, n, int(sh_degree), *ptrs, n_sg, p_sg, C.byref(opts), _stream(stream)), h)
+
+
+@_traced
+def rgx_image_loss(h, cams: Cameras, rgba, target, lam, loss, d_rgba, stream=None):
+    """loss [ncam] += (1 - lam) L1 + lam DSSIM per view; d_rgba [R,4] = dL/drgba (Sec. 3.4)."""
+    R = cams.n_rays
+    _same_device(rgba, target, loss, d_rgba)
+    _check(lib().rgx_image_loss(h, cams.ptr, cams.count, _ptr(rgba, "rgba", 4 * R, optional=False),
+                                _ptr(target, "target", 3 * R, optional=False), float(lam),
+                                _ptr(loss, "loss", cams.count, optional=False),
+                                _ptr(d_rgba, "d_rgba", 4 * R, optional=False), _stream(stream)), h)
+
+
+@_traced
+def rgx_adam_step(param, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-15, exp_param=False, activated=None,
+                  stream=None):
+    """One Adam step in place on `param` (and its moments m, v); see include/rgx.h."""
+    n = param.numel()
+    _same_device(param, grad, m, v, activated)
+    _check(lib().rgx_adam_step(n, _ptr(param, "param", n, optional=False), _ptr(grad, "grad", n, optional=False),
+                               _ptr(m, "m", n, optional=False), _ptr(v, "v", n, optional=False), float(lr),
+                               float(beta1), float(beta2), float(eps), int(step), int(bool(exp_param)),
+                               _ptr(activated, "activated", n), _stream(stream)))
+
+
+def rgx_densify_plan(h, stat, count, scales, tau, size_threshold, action, offset, stream=None) -> int:
+    """Clone / split decision per Gaussian (Eq. 11 criterion); returns the new Gaussian count."""
+    n = int(stat.numel())
+    _same_device(stat, count, scales, action, offset)
+    out = C.c_int64(0)
+    _check(lib().rgx_densify_plan(h, n, _ptr(stat, "stat", n), _ptr(count, "count", n, dtype=torch.int32),
+                                  _ptr(scales, "scales", 3 * n), float(tau), float(size_threshold),
+                                  _ptr(action, "action", n, dtype=torch.int32),
+                                  _ptr(offset, "offset", n, dtype=torch.int32), C.byref(out), _stream(stream)), h)
+    return int(out.value)
+
+
+@_traced
+def rgx_densify_apply(action, offset, normals, params, outs, sg=None, out_sg=None, out_src=None, stream=None):
+    """Write the kept, cloned and split Gaussians of a plan; params / outs are (means, scales,
+    quats, densities, sh) tensors, normals [n, 2, 3]."""
+    n = int(action.numel())
+    means, scales, quats, dens, sh = params
+    om, os_, oq, od, osh = outs
+    _same_device(action, offset, normals, *params, *outs, sg, out_sg, out_src)
+    shf = int(sh[0].numel()) if n > 0 else 0
+    sgf = int(sg[0].numel()) if (sg is not None and n > 0) else 0
+    _check(lib().rgx_densify_apply(n, _ptr(action, "action", n, dtype=torch.int32),
+                                   _ptr(offset, "offset", n, dtype=torch.int32), _ptr(normals, "normals", 6 * n),
+                                   _ptr(means, "means", 3 * n), _ptr(scales, "scales", 3 * n),
+                                   _ptr(quats, "quats", 4 * n), _ptr(dens, "densities", n), _ptr(sh, "sh", shf * n),
+                                   shf, _ptr(sg, "sg", sgf * n), sgf, _ptr(om, "out_means"), _ptr(os_, "out_scales"),
+                                   _ptr(oq, "out_quats"), _ptr(od, "out_densities"), _ptr(osh, "out_sh"),
+                                   _ptr(out_sg, "out_sg"), _ptr(out_src, "out_src", dtype=torch.int32),
+                                   _stream(stream)))
+
+
 def rgx_sync_status(h, stream=None) -> int:
     return int(lib().rgx_sync_status(h, _stream(stream)))
 
@@ -378,6 +479,7 @@ class Scene:
         self.h = rgx_scene_create(self.device)
         self.n = 0
         self.sh_degree = 3
+        self.n_sg = 0
         self._keep = None
 
     def __del__(self):
@@ -388,11 +490,16 @@ class Scene:
         except Exception:
             pass
 
-    def build(self, means, scales, quats, densities, sh, opts, sh_degree: int = 3, stream=None):
-        for t in (means, scales, quats, densities, sh):
+    def build(self, means, scales, quats, densities, sh, opts, sh_degree: int = 3, stream=None, sg=None):
+        for t in (means, scales, quats, densities, sh, sg):
             if isinstance(t, torch.Tensor) and t.is_cuda and t.device.index != self.device:
                 raise ValueError(f"parameters on {t.device}, scene on cuda:{self.device}")
-        rgx_build_bvh(self.h, means, scales, quats, densities, sh, sh_degree, opts, stream)
+        if sg is None:
+            rgx_build_bvh(self.h, means, scales, quats, densities, sh, sh_degree, opts, stream)
+            self.n_sg = 0
+        else:
+            rgx_build_bvh_sg(self.h, means, scales, quats, densities, sh, sh_degree, sg, opts, stream)
+            self.n_sg = int(sg.shape[1])
         self.n = int(means.shape[0])
         self.sh_degree = int(sh_degree)
 
@@ -413,6 +520,12 @@ class Scene:
         self._keep = cams
         rgx_render_backward(self.h, cams, opts, state, d_rgba, *grads, stream=stream, n=self.n,
                             sh_degree=self.sh_degree)
+
+    def backward_ex(self, cams: Cameras, opts, state, d_rgba, grads, d_sg=None, stat=None, count=None, stream=None):
+        """Adjoint with the lobe gradients (d_sg) and/or each camera's Eq. 11 statistic."""
+        self._keep = cams
+        rgx_render_backward_ex(self.h, cams, opts, state, d_rgba, *grads, d_sg=d_sg, stat=stat, count=count,
+                               stream=stream, n=self.n, sh_degree=self.sh_degree, n_sg=self.n_sg)
 
     def status(self, stream=None) -> int:
         return rgx_sync_status(self.h, stream)
@@ -451,3 +564,10 @@ def scene_tensors(scene, device="cuda"):
     nk = (scene.sh_degree + 1) ** 2
     return (t(scene.means).reshape(-1, 3), t(scene.scales).reshape(-1, 3), t(scene.quats).reshape(-1, 4),
             t(scene.densities).reshape(-1), t(scene.sh).reshape(-1, nk, 3))
+
+
+def sg_tensor(scene, device="cuda"):
+    """The scene's spherical-Gaussian lobes as a contiguous float32 CUDA tensor (or None)."""
+    if getattr(scene, "sg", None) is None:
+        return None
+    return torch.as_tensor(np.ascontiguousarray(scene.sg, dtype=np.float32), device=device).contiguous()

@@ -87,6 +87,7 @@ class Options:
     morton: bool = False        # store parameters in Z-order
     ztiles: bool = False        # Z-order 2D ray tiles
     morton63: bool = False      # 63-bit instead of 30-bit Morton codes
+    lower_first: bool = False   # scheduling: lower an overflowing first window instead of giving up
     dt: float = 0.01
     dt_min: float = 0.005
     dt_max: float = 0.02

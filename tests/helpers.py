@@ -15,13 +15,14 @@ TOL_GRAD = 1e-3      # relative L2 per parameter tensor
 def gpu_render(scene: synth.Scene, cams, opts, sched_cap: int = 0, scene_obj=None):
     sc = scene_obj or rgx.Scene()
     t = rgx.scene_tensors(scene)
+    sg = rgx.sg_tensor(scene)
     o = rgx.make_opts(opts)
-    sc.build(*t, o, sh_degree=scene.sh_degree)
+    sc.build(*t, o, sh_degree=scene.sh_degree, sg=sg)
     cb = rgx.Cameras(cams)
     out = sc.forward(cb, o, want_state=True, sched_cap=sched_cap)
     status = sc.status()
     res = dict(rgba=out[0].cpu().numpy().astype(np.float64), state=out[1], status=status, scene=sc,
-               cams=cb, opts=o, tensors=t)
+               cams=cb, opts=o, tensors=t, sg=sg)
     if sched_cap:
         res["sched"] = out[2].cpu().numpy().astype(np.float64)
         res["sched_n"] = out[3].cpu().numpy().astype(np.int64)
@@ -32,10 +33,18 @@ def gpu_backward(res, d_rgba: np.ndarray):
     sc, cb, o, t = res["scene"], res["cams"], res["opts"], res["tensors"]
     grads = [torch.zeros_like(x) for x in t]
     up = torch.as_tensor(np.ascontiguousarray(d_rgba, dtype=np.float32), device=t[0].device)
-    sc.backward(cb, o, res["state"], up, grads)
+    d_sg = None
+    if res.get("sg") is not None:
+        d_sg = torch.zeros_like(res["sg"])
+        sc.backward_ex(cb, o, res["state"], up, grads, d_sg=d_sg)
+    else:
+        sc.backward(cb, o, res["state"], up, grads)
     status = sc.status()
-    return dict(means=grads[0].cpu().numpy(), scales=grads[1].cpu().numpy(), quats=grads[2].cpu().numpy(),
-                densities=grads[3].cpu().numpy(), sh=grads[4].cpu().numpy(), status=status)
+    out = dict(means=grads[0].cpu().numpy(), scales=grads[1].cpu().numpy(), quats=grads[2].cpu().numpy(),
+               densities=grads[3].cpu().numpy(), sh=grads[4].cpu().numpy(), status=status)
+    if d_sg is not None:
+        out["sg"] = d_sg.cpu().numpy()
+    return out
 
 
 # (test, divergent pixels, pixels compared) of every comparison in the session; printed in the

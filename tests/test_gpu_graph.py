@@ -61,7 +61,8 @@ def test_autotune_picks_a_candidate_that_renders_the_same():
     assert ms > 0
     assert (best.tile_w, best.tile_h) in [(8, 4), (4, 8), (16, 2), (32, 1)]
     assert best.hit_cap in (128, 192, 256, 384, 512, 640, 768) and best.n_s == base.n_s
-    assert best.flags == base.flags and best.dt_min == base.dt_min
+    # the tuner may switch first-window lowering (scheduling only), nothing else of the flags
+    assert (best.flags & ~rgx.RGX_LOWER_FIRST) == (base.flags & ~rgx.RGX_LOWER_FIRST) and best.dt_min == base.dt_min
     sc.build(*t, base)
     a, _ = sc.forward(cams, base)
     b, _ = sc.forward(cams, best)

@@ -41,7 +41,8 @@ def test_zero_knobs_select_defaults_then_the_tuned_values():
     best, _ = sc.autotune(cams, zero, tune_ns=True, with_backward=False)
     assert best.hit_cap in (128, 192, 256, 384, 512, 640, 768) and best.n_s in (4, 8, 16, 32)
     tuned = rgx.make_opts(dataclasses.replace(w.options, hit_cap=best.hit_cap, tile_w=best.tile_w,
-                                              tile_h=best.tile_h, n_s=best.n_s))
+                                              tile_h=best.tile_h, n_s=best.n_s,
+                                              lower_first=bool(best.flags & rgx.RGX_LOWER_FIRST)))
     assert torch.equal(_render(sc, cams, zero), _render(sc, cams, tuned))
     # forward and adjoint with zero knobs resolve alike: the replay reproduces T (no RGX_ERR_REPLAY)
     rgba, state = sc.forward(cams, zero)

@@ -80,7 +80,7 @@ def test_batch_1m_one_launch_adjoint_matches_oracle_sum_over_views():
     d = np.zeros((int(offs[-1]), 4))
     per_view = []
     for ci, cam in enumerate(w.cameras):
-        pix = synth.pixel_subset(cam, 40, seed=300 + ci)
+        pix = synth.pixel_subset(cam, 24, seed=300 + ci)
         sl = slice(offs[ci], offs[ci + 1])
         ref = oracle.render(w.scene, cam, w.options, pix=pix, sched_cap=48, params=params)
         agree = schedules_agree(r["sched"][sl], r["sched_n"][sl], ref["sched"], ref["sched_n"], pix)
@@ -191,7 +191,7 @@ def test_tuned_segment_length_parity():
     best, ms = sc.autotune(rgx.Cameras([cam]), base, tune_ns=True, with_backward=True)
     assert ms > 0 and best.n_s in (4, 8, 16, 32)
     o = dataclasses.replace(w.options, n_s=int(best.n_s), hit_cap=int(best.hit_cap), tile_w=int(best.tile_w),
-                            tile_h=int(best.tile_h))
+                            tile_h=int(best.tile_h), lower_first=bool(best.flags & rgx.RGX_LOWER_FIRST))
     r = gpu_render(w.scene, [cam], o, sched_cap=128)
     assert r["status"] == 0
     params = oracle.Params(w.scene)

@@ -77,3 +77,62 @@ def test_whole_job_value_counts_every_rank_over_the_slowest_time():
     two = bench.whole_job_mrays(2, 640_000, 10, 300.0)
     assert np.isclose(two, 2 * 640_000 * 10 / 0.3 / 1e6)
     assert two < 2 * one
+
+
+def _allreduce_main(rank: int, world: int, port: int, q) -> None:
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2509_07782_b300 import dist as rdist
+    from paper_2509_07782_b300 import synth
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = synth.workload("plain_2k", n=300)
+        cam = synth.rescale_camera(_rank_camera(rank), 0.25)  # 16x16
+        W = np.random.default_rng(10 + rank).normal(size=(cam.n_rays, 4))
+        g = oracle.backward(w.scene, cam, w.options, W)
+        parts = [torch.as_tensor(g[k], dtype=torch.float64) for k in ("means", "scales", "quats", "densities", "sh")]
+        flat, views = rdist.flat_views(parts, "cpu", dtype=torch.float64)
+        for v, p in zip(views, parts):
+            v.copy_(p)
+        rdist.allreduce_gradients(flat, world)
+        q.put((rank, flat.numpy().copy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def _rank_camera(rank: int):
+    import bench
+    return bench.rank_workload("plain_2k", rank).cameras[0]
+
+
+def test_view_sharded_gradients_sum_over_ranks_with_one_allreduce():
+    """Each rank differentiates its own view (the oracle, on the host) and the
+    five gradient tensors, views of one flat buffer, are summed over the ranks
+    with one all-reduce: every rank ends with the gradient of both views."""
+    import oracle
+    from paper_2509_07782_b300 import synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_allreduce_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = dict(q.get(timeout=300) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = synth.workload("plain_2k", n=300)
+    total = []
+    for rank in range(2):
+        cam = synth.rescale_camera(_rank_camera(rank), 0.25)
+        W = np.random.default_rng(10 + rank).normal(size=(cam.n_rays, 4))
+        g = oracle.backward(w.scene, cam, w.options, W)
+        total.append(np.concatenate([g[k].ravel() for k in ("means", "scales", "quats", "densities", "sh")]))
+    ref = total[0] + total[1]
+    assert np.abs(ref).max() > 0
+    np.testing.assert_allclose(out[0], ref, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(out[1], ref, rtol=1e-12, atol=1e-12)
