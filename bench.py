@@ -93,6 +93,9 @@ def parse(argv=None):
     p.add_argument("--tile", default=None, help="fixed ray-tile shape WxH (skips rgx_autotune)")
     p.add_argument("--hit-cap", type=int, default=None, help="fixed hit-list capacity (skips rgx_autotune)")
     p.add_argument("--n-s", type=int, default=None, help="fixed samples per segment (skips rgx_autotune)")
+    p.add_argument("--scale-res", type=float, default=None,
+                   help="scale every view's resolution (a smaller case of the same scene, e.g. for a profiler "
+                        "capture; the line's config records it)")
     return p.parse_args(argv)
 
 
@@ -253,7 +256,7 @@ def batch_cameras(rank: int):
     return [synth.orbit_camera(rng, 4.0, w, h) for (w, h) in synth.BATCH_RES]
 
 
-def rank_workload(name: str, rank: int):
+def rank_workload(name: str, rank: int, scale_res=None):
     """The workload as rank `rank` renders it: rank 0 the named views, every other
     rank its own seeded views of the same scene (weak scaling)."""
     from paper_2509_07782_b300 import synth
@@ -269,6 +272,8 @@ def rank_workload(name: str, rank: int):
             w.cameras = batch_cameras(rank)
         else:
             w.cameras = [synth.orbit_camera(rng, 4.0, cam0.width, cam0.height)]
+    if scale_res is not None:
+        w.cameras = [synth.rescale_camera(c, scale_res) for c in w.cameras]
     return w
 
 
@@ -464,7 +469,7 @@ def run_step(args, name, rank, world, local, plain=True, e2e=True):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = rank_workload(name, rank)
+    w = rank_workload(name, rank, getattr(args, "scale_res", None))
     opts = rgx.make_opts(w.options)
     cams = rgx.Cameras(w.cameras)
     R = cams.n_rays
@@ -598,8 +603,7 @@ def run_sweep(args, steps=None):
     dev = torch.device("cuda", 0)
     steps = steps or args.steps
     w = synth.workload("sweep_6m")
-    opts = rgx.make_opts(w.options)
-    opts.hit_cap, opts.tile_w, opts.tile_h = 0, 0, 0   # the library's defaults (this scene is not tuned)
+    opts = rgx.make_opts(w.options)   # the workload's own knobs (8x4 tiles, hit_cap 256): not tuned here
     t = rgx.scene_tensors(w.scene, device=dev)
     sc = rgx.Scene(0)
     sc.build(*t, opts)
@@ -711,7 +715,8 @@ def step_line(args, r, world):
         "metric": METRIC, "value": r["value"], "unit": "Mrays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_label(args.workload),
+        "config": {"workload": workload_label(args.workload) +
+                   (f" (views scaled by {args.scale_res})" if args.scale_res else ""),
                    "rays_per_step_per_gpu": r["R"], "views": r["ncam"], "gaussians": r["n"],
                    "l2": "flushed (256 MiB write) between steps",
                    "parallelism": (f"{world} ranks, each its own seeded views of one scene; one all-reduce "

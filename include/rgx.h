@@ -238,8 +238,9 @@ rgx_status rgx_render_backward_ex(rgx_scene* scene, const rgx_camera* cams, int3
  * caller's scene and cameras.  Candidates: 4 tile shapes (8x4, 4x8, 16x2,
  * 32x1), hit_cap in {128,192,256,384,512,640,768}, and with RGX_TUNE_NS N_S in
  * {4,8,16,32} (else base->n_s).  By default the knobs are tuned one at a time
- * (tile shape at the base hit_cap, then hit_cap, then N_S, then RGX_LOWER_FIRST
- * toggled: at most 4+6+3+1 candidates); RGX_TUNE_EXHAUSTIVE times every combination.  Each candidate runs
+ * (tile shape at the base hit_cap, then hit_cap, the other tile shapes again if
+ * hit_cap moved, then N_S, then RGX_LOWER_FIRST toggled: at most 4+6+3+3+1
+ * candidates); RGX_TUNE_EXHAUSTIVE times every combination.  Each candidate runs
  * once to warm up and twice timed with CUDA events on `stream`, forward only or
  * forward + adjoint (with_backward != 0).  Knobs left at 0 in *base start from
  * the defaults.  The fastest options are written to *best (other fields copied

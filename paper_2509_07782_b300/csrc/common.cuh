@@ -87,6 +87,10 @@ struct rgx_scene {
     size_t tape_alloc = 0;         // entries allocated
     uint32_t tape_gen = 0, tape_tag = 0;  // tag of the forward call whose lists the tape holds
     int64_t tape_limit = -1;       // caller's cap on tape entries (< 0: hit_cap / 6 per ray)
+    float4* csums = nullptr;       // sums records of chunked segments (see MarchParams::csums)
+    size_t csum_alloc = 0;         // in float4
+    int csum_slots = 0;            // records per ray the next forward with a state uses
+    int csum_slots_last = 0, csum_ns_last = 0;  // layout of the last forward's records
     // the last rgx_autotune result: what tuning knobs left at 0 select
     int has_tuned = 0;
     int tuned_hit_cap = 0, tuned_tile_w = 0, tuned_tile_h = 0, tuned_n_s = 0, tuned_flags = 0;
@@ -98,7 +102,7 @@ struct rgx_scene {
     // launch-configuration cache: (kernel, dynamic smem) -> resident blocks/SM,
     // so that calls inside a CUDA-graph capture make no attribute queries
     struct LaunchCfg { const void* k; size_t smem; int occ; };
-    LaunchCfg cfg[32];
+    LaunchCfg cfg[64];
     int ncfg = 0;
     char last_error[256] = {0};
 };

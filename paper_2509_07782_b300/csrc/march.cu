@@ -38,7 +38,7 @@
 
 // Version of the march kernels: changed whenever their code changes, so that
 // profiler counters taken on an older version are not attributed to this one.
-#define RGX_MARCH_VERSION "m2-7"
+#define RGX_MARCH_VERSION "m2-9"
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
@@ -47,9 +47,17 @@
 #define STK_RES 152                                 // depth-first reserve: 3 x (4-wide depth bound 48) + 4
 #define SURV 160                                    // leaves awaiting their exact chord (< 32 left + 128 new)
 #define CUT 32                                      // child records of a tile's BVH cut
+#ifndef RGX_LEAN_REGS
+#define RGX_LEAN_REGS 168                           // registers per thread of the lean march kernel (12 warps/SM)
+#endif
+#ifndef SPILL_CAP
 #define SPILL_CAP 4096                              // adjoint: chunk entries kept per warp in global scratch
+#endif
+
 #define TAPE_CHUNK 2048                             // tape entries a warp reserves at a time
 #define TAPE_FULL 0xffffffffu                       // a warp's tape_base once a reservation has failed
+#define RGX_CSUM_SLOTS 8                            // chunked-segment sums records per ray
+#define RGX_CSUM_BUDGET (16ull << 30)               // bytes for those records
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -80,7 +88,10 @@ struct MarchParams {
                          // (log2 sigma~, colour), (t_in, t_out, packed index bits, 0); forward writes, adjoint reads
     uint32_t* tape_n;    // forward: entries used so far
     uint32_t tape_cap;   // capacity in entries (0: no tape)
-    uint32_t tape_tag;   // identifies the forward call whose lists the tape holds
+    uint32_t tape_tag;   // identifies the forward call whose lists the tape (and the sums records) hold
+    float4* csums;       // per (ray, chunked segment ordinal < csum_slots): N_S + 1 float4 -- the segment's
+                         // per-sample sums (sigma, S) as composited, then (hit count bits, 0, 0, 0)
+    uint32_t csum_slots; // records per ray (0: none)
     float2* sched;
     int sched_cap;
     int32_t* sched_n;
@@ -817,6 +828,9 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
     bool used_whole = false;  // the ray used a first window (recorded in the sign bit of its state)
     float first_hi = 0.0f;    // that window's end (recorded for the adjoint's taped replay)
     bool dense = false;  // the last evaluated segment overflowed the list: go straight to chunks
+    int kseg = 0;        // chunked segments so far (their sums records are kept in this order)
+    // adjoint: the forward of this state recorded the sums of its chunked segments
+    const bool csum_ok = BWD && P.csums != nullptr && P.csum_slots > 0 && st2.z == P.tape_tag;
     uint32_t tape_off = 0;
     int tape_cnt = -1;  // forward: where this ray's first-window list went on the tape (-1: not taped)
     float wlen = 4.0f * (float)NS * (uniform ? P.dt : P.dt_max);
@@ -978,6 +992,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
         // ---- the segment's hits and per-sample sums
         float sig = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
         int nexact = 0;
+        float4* seg_rec = nullptr;  // this chunked segment's sums record
         if (!chunked) {
             const uint32_t lt = lanemask_lt();
             // four 32-entry slices per step: all loads before the ballots
@@ -998,7 +1013,22 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             }
             __syncwarp();
             if (nexact) eval_entries<NS>(W, true, nexact, tS, dtk, true, sig, S0, S1, S2);
+        } else if (csum_ok && (uint32_t)kseg < P.csum_slots) {
+            // adjoint: the forward's sums of this chunked segment, as it composited them -- group 0
+            // holds them and the other lane groups zero, so the butterfly below reproduces them
+            // exactly -- instead of a traversal and every sample evaluated a second time; the
+            // gradients' pass traverses the segment once
+            const float4* rec = P.csums + ((size_t)ray * P.csum_slots + kseg) * (NS + 1);
+            const float4 v = lane < NS ? rec[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sig = v.x; S0 = v.y; S1 = v.z; S2 = v.w;
+            nexact = __float_as_int(rec[NS].x);
+            spill_ok = false;
+            nL = 0;
+            kseg++;
         } else {
+            if (!BWD && P.csums && (uint32_t)kseg < P.csum_slots)
+                seg_rec = P.csums + ((size_t)ray * P.csum_slots + kseg) * (NS + 1);
+            kseg++;
             int tot = 0;
             auto onfull = [&](int m) {
                 eval_entries<NS>(W, false, m, tS, dtk, true, sig, S0, S1, S2);
@@ -1024,6 +1054,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             if (nL) onfull(nL);
             nexact = tot;
             nL = 0;
+            if (seg_rec && lane == 0) seg_rec[NS] = make_float4(__int_as_float(tot), 0.f, 0.f, 0.f);
         }
         // chunks stay in use while segments keep more than half a list of hits
         dense = chunked && 2 * nexact > cap;
@@ -1068,6 +1099,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             S1 = __fadd_rn(S1, __shfl_xor_sync(FULLMASK, S1, off));
             S2 = __fadd_rn(S2, __shfl_xor_sync(FULLMASK, S2, off));
         }
+        if (!BWD && seg_rec && lane < NS) seg_rec[lane] = make_float4(sig, S0, S1, S2);
         // ---- front-to-back compositing of the N_S samples (Eq. 3)
         const float t0 = __fadd_rn(tS, __fmul_rn(0.5f, dtk));
         const float tk = __fmaf_rn((float)k, dtk, t0);
@@ -1313,7 +1345,7 @@ __device__ void build_cut(const MarchParams& P, const WS& W, const Frustum& F, C
 }
 
 template <int NS, bool BWD>
-__global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
+__device__ __forceinline__ void march_kernel(const MarchParams& P) {
     extern __shared__ __align__(16) unsigned char smem[];
     uint32_t* s_tiles = (uint32_t*)smem;         // [ncam+1] work-item prefix
     uint32_t* s_pix = s_tiles + (P.ncam + 1);    // [ncam+1] pixel prefix
@@ -1445,6 +1477,21 @@ __global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
     }
 }
 
+// The march kernel in two register budgets.  Without a cap the compiler takes up to ~240
+// registers per thread, so registers allow 8 one-warp blocks per SM -- as many as the shared
+// memory of a large chord list (hit_cap 512) does.  With short lists (dense scenes) shared
+// memory would allow more: k_march_lean is capped at RGX_LEAN_REGS registers (12 warps per SM,
+// with a few bytes of spills), and the host picks it when it really gets more warps.
+template <int NS, bool BWD>
+__global__ void __launch_bounds__(RGX_BLOCK, 1) k_march(MarchParams P) {
+    march_kernel<NS, BWD>(P);
+}
+
+template <int NS, bool BWD>
+__global__ void __maxnreg__(RGX_LEAN_REGS) k_march_lean(MarchParams P) {
+    march_kernel<NS, BWD>(P);
+}
+
 // Per-Gaussian chain of the accumulated local-frame moments to the caller's
 // parameters (packed index p -> caller index l):
 //   dsigma~ = A0 / sigma~,  dmu = M^T V,  ds_j = P_jj / s_j,
@@ -1501,14 +1548,14 @@ __global__ void k_grad_finalize(int64_t n, int morton, int nk, const float4* __r
 
 // ------------------------------------------------------------------ host side
 template <int NS, bool BWD>
-static void* kernel_ptr() { return (void*)k_march<NS, BWD>; }
+static void* kernel_ptr(bool lean) { return lean ? (void*)k_march_lean<NS, BWD> : (void*)k_march<NS, BWD>; }
 
-static void* pick_kernel(int ns, bool bwd) {
+static void* pick_kernel(int ns, bool bwd, bool lean) {
     switch (ns) {
-        case 4: return bwd ? kernel_ptr<4, true>() : kernel_ptr<4, false>();
-        case 8: return bwd ? kernel_ptr<8, true>() : kernel_ptr<8, false>();
-        case 16: return bwd ? kernel_ptr<16, true>() : kernel_ptr<16, false>();
-        case 32: return bwd ? kernel_ptr<32, true>() : kernel_ptr<32, false>();
+        case 4: return bwd ? kernel_ptr<4, true>(lean) : kernel_ptr<4, false>(lean);
+        case 8: return bwd ? kernel_ptr<8, true>(lean) : kernel_ptr<8, false>(lean);
+        case 16: return bwd ? kernel_ptr<16, true>(lean) : kernel_ptr<16, false>(lean);
+        case 32: return bwd ? kernel_ptr<32, true>(lean) : kernel_ptr<32, false>(lean);
     }
     return nullptr;
 }
@@ -1581,30 +1628,56 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     P.min_items = 16u * (uint32_t)s->num_sms;
     RGX_CUDA(s, cudaMemcpyAsync(s->cams, cams, sizeof(rgx_camera) * ncam, cudaMemcpyHostToDevice, st));
     RGX_CUDA(s, cudaMemsetAsync(s->queue, 0, sizeof(unsigned), st));
-    // first-window tape: the forward (with a state to hand on) fills it, the adjoint reads it
-    if (!bwd && state && s->tape_cap > 0) {
+    // first-window tape and chunked-segment sums: the forward (with a state to hand on) fills
+    // them under a new tag, the adjoint reads them for states carrying that tag
+    if (!bwd && state) {
         s->tape_gen++;
         uint32_t tag = (uint32_t)(((uintptr_t)s >> 6) * 0x9E3779B1u) ^ (s->tape_gen * 0x85EBCA77u);
         s->tape_tag = tag ? tag : 1u;
-        RGX_CUDA(s, cudaMemsetAsync(s->queue + 1, 0, sizeof(unsigned), st));
-        P.tape = s->tape; P.tape_n = s->queue + 1; P.tape_cap = (uint32_t)s->tape_cap; P.tape_tag = s->tape_tag;
-    } else if (bwd && s->tape_cap > 0 && s->tape_tag != 0) {
-        P.tape = s->tape; P.tape_cap = (uint32_t)s->tape_cap; P.tape_tag = s->tape_tag;
+        P.tape_tag = s->tape_tag;
+        if (s->tape_cap > 0) {
+            RGX_CUDA(s, cudaMemsetAsync(s->queue + 1, 0, sizeof(unsigned), st));
+            P.tape = s->tape; P.tape_n = s->queue + 1; P.tape_cap = (uint32_t)s->tape_cap;
+        }
+        s->csum_slots_last = s->csum_slots;
+        s->csum_ns_last = o->n_s;
+        if (s->csum_slots > 0) { P.csums = s->csums; P.csum_slots = (uint32_t)s->csum_slots; }
+    } else if (bwd && s->tape_tag != 0) {
+        P.tape_tag = s->tape_tag;
+        if (s->tape_cap > 0) { P.tape = s->tape; P.tape_cap = (uint32_t)s->tape_cap; }
+        if (s->csum_slots_last > 0 && s->csum_ns_last == o->n_s) {
+            P.csums = s->csums;
+            P.csum_slots = (uint32_t)s->csum_slots_last;
+        }
     }
     RGX_CUDA(s, cudaMemsetAsync(s->counters, 0, 8 * sizeof(unsigned long long), st));
-    void* k = pick_kernel(o->n_s, bwd);
     const size_t head = ((size_t)(3 * (ncam + 1)) * 4 + 15) & ~(size_t)15;
     const size_t smem = head + (size_t)WARPS * warp_bytes(o->hit_cap, bwd);
-    int occ = 0;
-    for (int i = 0; i < s->ncfg; i++)
-        if (s->cfg[i].k == k && s->cfg[i].smem == smem) occ = s->cfg[i].occ;
-    if (occ == 0) {
-        RGX_CUDA(s, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        RGX_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, RGX_BLOCK, smem));
-        if (occ < 1) occ = 1;
-        const int slot = s->ncfg < 32 ? s->ncfg++ : 31;
-        s->cfg[slot] = {k, smem, occ};
-    }
+    // resident blocks per SM of a kernel at this shared-memory size (cached: no attribute query
+    // inside a CUDA-graph capture once a configuration has been seen)
+    auto occupancy = [&](void* kk, int* occ_out) -> rgx_status {
+        int occ = 0;
+        for (int i = 0; i < s->ncfg; i++)
+            if (s->cfg[i].k == kk && s->cfg[i].smem == smem) occ = s->cfg[i].occ;
+        if (occ == 0) {
+            RGX_CUDA(s, cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            RGX_CUDA(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kk, RGX_BLOCK, smem));
+            if (occ < 1) occ = 1;
+            const int slot = s->ncfg < 64 ? s->ncfg++ : 63;
+            s->cfg[slot] = {kk, smem, occ};
+        }
+        *occ_out = occ;
+        return RGX_OK;
+    };
+    void* k = pick_kernel(o->n_s, bwd, false);
+    void* kl = pick_kernel(o->n_s, bwd, true);
+    int occ = 0, occl = 0;
+    rgx_status rs = occupancy(k, &occ);
+    if (rs) return rs;
+    rs = occupancy(kl, &occl);
+    if (rs) return rs;
+    // the lean kernel only where it gains at least two warps per SM (its spills cost a little)
+    if (occl >= occ + 2) { k = kl; occ = occl; }
     if (occ < 1) occ = 1;
     const int grid = s->num_sms * occ;
 
@@ -1623,6 +1696,7 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
     }
     void* args[] = {&P};
     RGX_CUDA(s, cudaLaunchKernel(k, dim3(grid), dim3(RGX_BLOCK), args, smem, st));
+
     return RGX_OK;
 }
 
@@ -1668,6 +1742,20 @@ static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t n
             else { s->tape = nullptr; cudaGetLastError(); }
         }
         s->tape_cap = s->tape_alloc < need ? s->tape_alloc : need;
+        // sums records of chunked segments: up to RGX_CSUM_SLOTS per ray within RGX_CSUM_BUDGET bytes
+        // (none when the tape is disabled); rays with more chunked segments re-evaluate the rest
+        const size_t per_slot = (size_t)(o->n_s + 1) * sizeof(float4);
+        size_t slots = s->tape_limit == 0 ? 0 : (size_t)RGX_CSUM_BUDGET / ((size_t)R * per_slot + 1);
+        if (slots > RGX_CSUM_SLOTS) slots = RGX_CSUM_SLOTS;
+        const size_t cneed = slots * (size_t)R * (size_t)(o->n_s + 1);
+        if (slots > 0 && s->csum_alloc < cneed) {
+            if (s->csums) cudaFree(s->csums);
+            s->csums = nullptr;
+            s->csum_alloc = 0;
+            if (cudaMalloc(&s->csums, cneed * sizeof(float4)) == cudaSuccess) s->csum_alloc = cneed;
+            else { s->csums = nullptr; cudaGetLastError(); }
+        }
+        s->csum_slots = (s->csums && s->csum_alloc >= cneed) ? (int)slots : 0;
     }
     return launch_march(s, cams, ncam, o, false, rgba, state, nullptr, sched, sched_cap, sched_n,
                         (cudaStream_t)stream);

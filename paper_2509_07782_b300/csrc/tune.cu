@@ -55,7 +55,8 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
     float* const g[5] = {d_means, d_scales, d_quats, d_dens, d_sh};
     const int tiles[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
     const int ntiles = (base->flags & RGX_ZTILES) ? 4 : 1;
-    const int caps[7] = {128, 192, 256, 384, 512, 640, 768};
+    const int caps[9] = {64, 96, 128, 192, 256, 384, 512, 640, 768};
+    const int ncaps = 9;
     const int nss[4] = {4, 8, 16, 32};
     const bool tune_ns = (mode & RGX_TUNE_NS) != 0;
     // knobs left at 0 in base start from the defaults (not from an earlier tuning)
@@ -79,7 +80,7 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
         // every (tile shape, hit_cap[, N_S], first-window lowering) combination
         const int nlow = (base->flags & RGX_SKIP) ? 2 : 1;
         for (int ti = 0; ti < ntiles; ti++)
-            for (int ci = 0; ci < 7; ci++)
+            for (int ci = 0; ci < ncaps; ci++)
                 for (int ni = 0; ni < (tune_ns ? 4 : 1); ni++)
                     for (int li = 0; li < nlow; li++) {
                         rgx_opts o = b0;
@@ -98,11 +99,22 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
             consider(o);
         }
         const rgx_opts t1 = bo;
-        for (int ci = 0; ci < 7; ci++) {
+        for (int ci = 0; ci < ncaps; ci++) {
             if (caps[ci] == t1.hit_cap) continue;
             rgx_opts o = t1;
             o.hit_cap = caps[ci];
             consider(o);
+        }
+        if (bo.hit_cap != t1.hit_cap) {
+            // the best tile shape can change with the list capacity: the others again at the new one
+            const rgx_opts t1b = bo;
+            for (int ti = 0; ti < ntiles; ti++) {
+                if (tiles[ti][0] == t1b.tile_w && tiles[ti][1] == t1b.tile_h) continue;
+                rgx_opts o = t1b;
+                o.tile_w = tiles[ti][0];
+                o.tile_h = tiles[ti][1];
+                consider(o);
+            }
         }
         if (tune_ns) {
             const rgx_opts t2 = bo;
