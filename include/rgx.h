@@ -236,7 +236,7 @@ rgx_status rgx_render_backward_ex(rgx_scene* scene, const rgx_camera* cams, int3
  * capacity of the hit-primitive buffer H_b (hit_cap) -- and of the 2D ray
  * tiles of Sec. 3.3 (tile_w x tile_h, when RGX_ZTILES is set), timed on the
  * caller's scene and cameras.  Candidates: 4 tile shapes (8x4, 4x8, 16x2,
- * 32x1), hit_cap in {128,192,256,384,512,640,768}, and with RGX_TUNE_NS N_S in
+ * 32x1), hit_cap in {32,64,96,128,192,256,384,512,640,768}, and with RGX_TUNE_NS N_S in
  * {4,8,16,32} (else base->n_s).  By default the knobs are tuned one at a time
  * (tile shape at the base hit_cap, then hit_cap, the other tile shapes again if
  * hit_cap moved, then N_S, then RGX_LOWER_FIRST toggled: at most 4+6+3+3+1

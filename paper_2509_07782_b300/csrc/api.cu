@@ -33,7 +33,7 @@ extern "C" rgx_status rgx_scene_destroy(rgx_scene* s) {
     cudaSetDevice(s->device);
     void* ptrs[] = {s->keys[0], s->keys[1], s->vals[0], s->vals[1], s->hist, s->nodes, s->nodew, s->parent, s->visit,
                     s->geom, s->shc, s->aux, s->perm, s->leafbox, s->bounds, s->root, s->grad, s->cams,
-                    s->queue, s->status, s->counters, s->spill, s->tape, s->vgrad, s->sgp, s->gsg, s->loss_ws, s->plan_ws, s->csums};
+                    s->queue, s->status, s->counters, s->spill, s->tape, s->vgrad, s->sgp, s->gsg, s->loss_ws, s->plan_ws, s->csums, s->ptape};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete s;

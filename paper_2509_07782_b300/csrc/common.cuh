@@ -91,6 +91,8 @@ struct rgx_scene {
     size_t csum_alloc = 0;         // in float4
     int csum_slots = 0;            // records per ray the next forward with a state uses
     int csum_slots_last = 0, csum_ns_last = 0;  // layout of the last forward's records
+    uint32_t* ptape = nullptr;     // chord indices of recorded chunked segments
+    size_t ptape_alloc = 0, ptape_cap = 0, ptape_cap_last = 0;  // entries: allocated / next forward / last forward
     // the last rgx_autotune result: what tuning knobs left at 0 select
     int has_tuned = 0;
     int tuned_hit_cap = 0, tuned_tile_w = 0, tuned_tile_h = 0, tuned_n_s = 0, tuned_flags = 0;

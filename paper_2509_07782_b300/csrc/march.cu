@@ -38,7 +38,7 @@
 
 // Version of the march kernels: changed whenever their code changes, so that
 // profiler counters taken on an older version are not attributed to this one.
-#define RGX_MARCH_VERSION "m2-9"
+#define RGX_MARCH_VERSION "m2-10"
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
@@ -57,7 +57,10 @@
 #define TAPE_CHUNK 2048                             // tape entries a warp reserves at a time
 #define TAPE_FULL 0xffffffffu                       // a warp's tape_base once a reservation has failed
 #define RGX_CSUM_SLOTS 8                            // chunked-segment sums records per ray
+#define PTAPE_BLOCK 65536                           // chord indices a warp reserves at a time
+#define PTAPE_MIN_FREE 4096                         // a chunked segment starts a new block below this much room
 #define RGX_CSUM_BUDGET (16ull << 30)               // bytes for those records
+#define RGX_PTAPE_MAX (4000000000ull)               // entries of the index tape at most (16 GB; 32-bit offsets)
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -92,6 +95,9 @@ struct MarchParams {
     float4* csums;       // per (ray, chunked segment ordinal < csum_slots): N_S + 1 float4 -- the segment's
                          // per-sample sums (sigma, S) as composited, then (hit count bits, 0, 0, 0)
     uint32_t csum_slots; // records per ray (0: none)
+    uint32_t* ptape;     // packed indices of recorded chunked segments' chords, in the order the forward met them
+    uint32_t* ptape_n;   // forward: entries reserved so far (per-warp blocks of PTAPE_BLOCK)
+    uint32_t ptape_cap;  // capacity in entries (0: none)
     float2* sched;
     int sched_cap;
     int32_t* sched_n;
@@ -789,7 +795,8 @@ template <int NS, bool BWD>
 __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int cam, const rgx_camera& C, int px, int py,
                           const float4& root_lo, const float4& root_hi, const float4& up, const float4& st,
                           const uint4& st2, Counters& cnt, bool& whole, uint32_t& tape_base,
-                          uint32_t& tape_left, float4& o_rgba, float4& o_state, uint4& o_tape, int& o_nrec) {
+                          uint32_t& tape_left, uint32_t& pt_base, uint32_t& pt_left, float4& o_rgba,
+                          float4& o_state, uint4& o_tape, int& o_nrec) {
     const int lane = threadIdx.x & 31;
     const int k = lane % NS;
     const int cap = P.hit_cap;
@@ -993,6 +1000,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
         float sig = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
         int nexact = 0;
         float4* seg_rec = nullptr;  // this chunked segment's sums record
+        uint32_t pid_off = TAPE_FULL;  // adjoint: where the segment's chord indices start on the index tape
         if (!chunked) {
             const uint32_t lt = lanemask_lt();
             // four 32-entry slices per step: all loads before the ballots
@@ -1021,7 +1029,10 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             const float4* rec = P.csums + ((size_t)ray * P.csum_slots + kseg) * (NS + 1);
             const float4 v = lane < NS ? rec[lane] : make_float4(0.f, 0.f, 0.f, 0.f);
             sig = v.x; S0 = v.y; S1 = v.z; S2 = v.w;
-            nexact = __float_as_int(rec[NS].x);
+            const float4 hd = rec[NS];
+            nexact = __float_as_int(hd.x);
+            // the segment's chords by index, when the forward could tape them
+            if (P.ptape && __float_as_uint(hd.z) != 0u) pid_off = __float_as_uint(hd.y);
             spill_ok = false;
             nL = 0;
             kseg++;
@@ -1029,9 +1040,35 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             if (!BWD && P.csums && (uint32_t)kseg < P.csum_slots)
                 seg_rec = P.csums + ((size_t)ray * P.csum_slots + kseg) * (NS + 1);
             kseg++;
+            // forward: the chords of a recorded segment also go to the index tape, contiguously in
+            // this warp's block (a new block when little room is left; none when the tape is full)
+            bool pt_ok = false;
+            if (!BWD && seg_rec && P.ptape) {
+                if (pt_left < PTAPE_MIN_FREE && pt_base != TAPE_FULL) {
+                    uint32_t base = TAPE_FULL;
+                    if (lane == 0 && *(volatile uint32_t*)P.ptape_n < P.ptape_cap)
+                        base = atomicAdd(P.ptape_n, (uint32_t)PTAPE_BLOCK);
+                    base = __shfl_sync(FULLMASK, base, 0);
+                    if (base != TAPE_FULL && (uint64_t)base + PTAPE_BLOCK <= (uint64_t)P.ptape_cap) {
+                        pt_base = base;
+                        pt_left = PTAPE_BLOCK;
+                    } else {
+                        pt_base = TAPE_FULL;
+                        pt_left = 0;
+                    }
+                }
+                pt_ok = pt_base != TAPE_FULL && pt_left > 0;
+            }
             int tot = 0;
             auto onfull = [&](int m) {
                 eval_entries<NS>(W, false, m, tS, dtk, true, sig, S0, S1, S2);
+                if (!BWD && pt_ok) {
+                    if ((uint32_t)(tot + m) <= pt_left) {
+                        for (int e = lane; e < m; e += 32) P.ptape[pt_base + (uint32_t)tot + e] = W.pid[e];
+                    } else {
+                        pt_ok = false;
+                    }
+                }
                 if (BWD && spill_ok) {
                     // keep the chunk for the adjoint pass (no second traversal)
                     if (tot + m <= SPILL_CAP) {
@@ -1054,7 +1091,13 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             if (nL) onfull(nL);
             nexact = tot;
             nL = 0;
-            if (seg_rec && lane == 0) seg_rec[NS] = make_float4(__int_as_float(tot), 0.f, 0.f, 0.f);
+            if (seg_rec && lane == 0)
+                seg_rec[NS] = make_float4(__int_as_float(tot), __uint_as_float(pt_ok ? pt_base : 0u),
+                                          __uint_as_float(pt_ok ? 1u : 0u), 0.f);
+            if (!BWD && pt_ok) {
+                pt_base += (uint32_t)tot;
+                pt_left -= (uint32_t)tot;
+            }
         }
         // chunks stay in use while segments keep more than half a list of hits
         dense = chunked && 2 * nexact > cap;
@@ -1160,6 +1203,22 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
                         W.pid[e] = __float_as_uint(d[2].x);
                     }
                     __syncwarp();
+                    adjoint_flush<NS>(P, W, r, false, m, tS, dtk, 0, NS, cam);
+                }
+            } else if (pid_off != TAPE_FULL) {
+                // the chords the forward taped by index, in its order: solved and coloured again
+                // (the same rounded arithmetic) without a traversal
+                for (int b = 0; b < nexact; b += cap) {
+                    const int m = min(cap, nexact - b);
+                    for (int e = lane; e < m; e += 32) {
+                        const uint32_t q = P.ptape[pid_off + (uint32_t)(b + e)];
+                        const Chord ch = chord_of(P.geom, q, r);
+                        W.q[e] = make_float4(ch.tc, ch.a, ch.qmin, ch.Qe);
+                        W.c[e] = make_float4(ch.L, 0.f, 0.f, 0.f);
+                        W.pid[e] = q;
+                    }
+                    __syncwarp();
+                    colour_entries(P, W, r, 0, m);
                     adjoint_flush<NS>(P, W, r, false, m, tS, dtk, 0, NS, cam);
                 }
             } else {
@@ -1376,6 +1435,7 @@ __device__ __forceinline__ void march_kernel(const MarchParams& P) {
     const float4 root_lo = make_float4(P.root[0], P.root[1], P.root[2], 0.f);
     const float4 root_hi = make_float4(P.root[3], P.root[4], P.root[5], 0.f);
     uint32_t tape_base = 0, tape_left = 0;  // forward: this warp's current chunk of the tape
+    uint32_t pt_base = 0, pt_left = 0;      // forward: this warp's current block of the index tape
     while (true) {
         uint32_t t = 0;
         if (lane == 0) t = atomicAdd(P.queue, 1u);
@@ -1445,7 +1505,7 @@ __device__ __forceinline__ void march_kernel(const MarchParams& P) {
                                    __shfl_sync(FULLMASK, my_st2.z, l), __shfl_sync(FULLMASK, my_st2.w, l));
             }
             march_ray<NS, BWD>(P, W, ray, c, cam, px, py, root_lo, root_hi, up_l, st_l, st2_l, cnt, whole, tape_base,
-                               tape_left, o_rgba, o_state, o_tape, o_nrec);
+                               tape_left, pt_base, pt_left, o_rgba, o_state, o_tape, o_nrec);
             if (!BWD && lane == l) { my_rgba = o_rgba; my_state = o_state; my_tape = o_tape; my_nrec = o_nrec; }
         }
         if (!BWD) {
@@ -1642,12 +1702,19 @@ static rgx_status launch_march(rgx_scene* s, const rgx_camera* cams, int32_t nca
         s->csum_slots_last = s->csum_slots;
         s->csum_ns_last = o->n_s;
         if (s->csum_slots > 0) { P.csums = s->csums; P.csum_slots = (uint32_t)s->csum_slots; }
+        s->ptape_cap_last = 0;
+        if (s->csum_slots > 0 && s->ptape_cap > 0) {
+            RGX_CUDA(s, cudaMemsetAsync(s->queue + 2, 0, sizeof(unsigned), st));
+            P.ptape = s->ptape; P.ptape_n = s->queue + 2; P.ptape_cap = (uint32_t)s->ptape_cap;
+            s->ptape_cap_last = s->ptape_cap;
+        }
     } else if (bwd && s->tape_tag != 0) {
         P.tape_tag = s->tape_tag;
         if (s->tape_cap > 0) { P.tape = s->tape; P.tape_cap = (uint32_t)s->tape_cap; }
         if (s->csum_slots_last > 0 && s->csum_ns_last == o->n_s) {
             P.csums = s->csums;
             P.csum_slots = (uint32_t)s->csum_slots_last;
+            if (s->ptape_cap_last > 0) { P.ptape = s->ptape; P.ptape_cap = (uint32_t)s->ptape_cap_last; }
         }
     }
     RGX_CUDA(s, cudaMemsetAsync(s->counters, 0, 8 * sizeof(unsigned long long), st));
@@ -1756,6 +1823,17 @@ static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t n
             else { s->csums = nullptr; cudaGetLastError(); }
         }
         s->csum_slots = (s->csums && s->csum_alloc >= cneed) ? (int)slots : 0;
+        // the index tape of the recorded segments' chords: up to 512 per ray within its budget
+        size_t pneed = s->csum_slots > 0 ? (size_t)R * 512 : 0;
+        if (pneed > (size_t)RGX_PTAPE_MAX) pneed = (size_t)RGX_PTAPE_MAX;
+        if (pneed > 0 && s->ptape_alloc < pneed) {
+            if (s->ptape) cudaFree(s->ptape);
+            s->ptape = nullptr;
+            s->ptape_alloc = 0;
+            if (cudaMalloc(&s->ptape, pneed * sizeof(uint32_t)) == cudaSuccess) s->ptape_alloc = pneed;
+            else { s->ptape = nullptr; cudaGetLastError(); }
+        }
+        s->ptape_cap = (s->ptape && s->ptape_alloc >= pneed) ? pneed : 0;
     }
     return launch_march(s, cams, ncam, o, false, rgba, state, nullptr, sched, sched_cap, sched_n,
                         (cudaStream_t)stream);

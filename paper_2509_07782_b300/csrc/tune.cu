@@ -55,8 +55,8 @@ extern "C" rgx_status rgx_autotune(rgx_scene* s, const rgx_camera* cams, int32_t
     float* const g[5] = {d_means, d_scales, d_quats, d_dens, d_sh};
     const int tiles[4][2] = {{8, 4}, {4, 8}, {16, 2}, {32, 1}};
     const int ntiles = (base->flags & RGX_ZTILES) ? 4 : 1;
-    const int caps[9] = {64, 96, 128, 192, 256, 384, 512, 640, 768};
-    const int ncaps = 9;
+    const int caps[10] = {32, 64, 96, 128, 192, 256, 384, 512, 640, 768};
+    const int ncaps = 10;
     const int nss[4] = {4, 8, 16, 32};
     const bool tune_ns = (mode & RGX_TUNE_NS) != 0;
     // knobs left at 0 in base start from the defaults (not from an earlier tuning)

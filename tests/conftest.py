@@ -16,10 +16,14 @@ def pytest_configure(config):
 def pytest_terminal_summary(terminalreporter):
     """Rounding-divergent segment decisions seen by the GPU parity comparisons."""
     try:
-        from helpers import DIVERGENCE_LOG
+        from helpers import DIVERGENCE_LOG, PARITY_LOG
     except Exception:
         return
     if DIVERGENCE_LOG:
         terminalreporter.write_sep("-", "pixels with a rounding-divergent decision (accepted by schedule replay)")
         for name, nd, n in DIVERGENCE_LOG:
             terminalreporter.write_line(f"{name}: {nd} of {n}")
+    if PARITY_LOG:
+        terminalreporter.write_sep("-", "parity against the FP64 oracle (tolerances: RGBA 1e-4, gradients 1e-3)")
+        for name, q, v in PARITY_LOG:
+            terminalreporter.write_line(f"{name}: {q} {v:.3g}")

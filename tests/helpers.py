@@ -55,8 +55,16 @@ DIVERGENCE_LOG = []
 MAX_DIVERGENT_FRAC = 0.001
 
 
+# (test, quantity, value) of the parity comparisons: max-abs RGBA error, worst relative L2 per gradient tensor
+PARITY_LOG = []
+
+
 def record_divergence(name: str, ndiv: int, n: int):
     DIVERGENCE_LOG.append((name, int(ndiv), int(n)))
+
+
+def record_parity(name: str, quantity: str, value: float):
+    PARITY_LOG.append((name, quantity, float(value)))
 
 
 def compare_rgba(gpu_rgba: np.ndarray, cam, scene, opts, pix=None, gpu_sched=None, gpu_sched_n=None,

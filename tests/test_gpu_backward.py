@@ -13,14 +13,14 @@ import pytest
 
 import oracle
 from paper_2509_07782_b300 import synth
-from helpers import TOL_GRAD, gpu_backward, gpu_render, rel_l2, schedules_agree
+from helpers import TOL_GRAD, gpu_backward, gpu_render, record_parity, rel_l2, schedules_agree
 
 pytestmark = pytest.mark.gpu
 
 NAMES = ["means", "scales", "quats", "densities", "sh"]
 
 
-def run_case(scene, cam, opts, pix, sched_cap=64, params=None):
+def run_case(scene, cam, opts, pix, sched_cap=64, params=None, label=None):
     r = gpu_render(scene, [cam], opts, sched_cap=sched_cap)
     assert r["status"] == 0
     ref = oracle.render(scene, cam, opts, pix=pix, sched_cap=sched_cap, params=params)
@@ -34,6 +34,8 @@ def run_case(scene, cam, opts, pix, sched_cap=64, params=None):
     assert g["status"] == 0, f"device status {g['status']}"
     gr = oracle.backward(scene, cam, opts, W, pix=pix, params=params)
     errs = {k: rel_l2(g[k], gr[k]) for k in NAMES}
+    record_parity(f"{label or 'adjoint'} ({cam.width}x{cam.height}, {len(pix)} px)", "worst gradient rel L2",
+                  max(errs.values()))
     for k in NAMES:
         assert np.linalg.norm(gr[k]) > 0, k
         assert errs[k] <= TOL_GRAD, f"{k}: rel L2 {errs[k]:.3g} ({errs})"
@@ -43,20 +45,20 @@ def run_case(scene, cam, opts, pix, sched_cap=64, params=None):
 def test_plain_2k_full_frame_gradients():
     w = synth.workload("plain_2k")
     cam = w.cameras[0]
-    run_case(w.scene, cam, w.options, np.arange(cam.n_rays))
+    run_case(w.scene, cam, w.options, np.arange(cam.n_rays), label="plain_2k uniform")
 
 
 def test_fast_options_small_gradients():
     w = synth.workload("plain_2k")
     cam = w.cameras[0]
-    run_case(w.scene, cam, synth.fast_options(dt=0.01), np.arange(cam.n_rays))
+    run_case(w.scene, cam, synth.fast_options(dt=0.01), np.arange(cam.n_rays), label="plain_2k fast options")
 
 
 def test_torus_100k_bench_configuration_gradients():
     w = synth.workload("torus_100k")
     cam = w.cameras[0]
     pix = synth.pixel_subset(cam, 4096, seed=7)
-    run_case(w.scene, cam, w.options, pix, params=oracle.Params(w.scene))
+    run_case(w.scene, cam, w.options, pix, params=oracle.Params(w.scene), label="torus_100k")
 
 
 def test_outdoor_gradients_sampled():

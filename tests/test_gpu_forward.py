@@ -18,7 +18,7 @@ import pytest
 
 import oracle
 from paper_2509_07782_b300 import synth
-from helpers import MAX_DIVERGENT_FRAC, TOL_RGBA, compare_rgba, gpu_render, record_divergence
+from helpers import MAX_DIVERGENT_FRAC, TOL_RGBA, compare_rgba, gpu_render, record_divergence, record_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -28,6 +28,7 @@ def test_plain_2k_full_frame():
     r = gpu_render(w.scene, w.cameras, w.options)
     assert r["status"] == 0
     err, ndiv = compare_rgba(r["rgba"], w.cameras[0], w.scene, w.options)
+    record_parity("plain_2k full frame", "max-abs RGBA", err)
     assert err <= TOL_RGBA and ndiv == 0
     assert r["rgba"][:, 3].max() > 0.9
 
@@ -64,6 +65,7 @@ def test_torus_100k_bench_configuration_sampled():
     err, ndiv = compare_rgba(r["rgba"], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"],
                              gpu_sched_n=r["sched_n"])
     record_divergence("torus_100k, bench configuration", ndiv, len(pix))
+    record_parity("torus_100k, 4096 px", "max-abs RGBA", err)
     assert err <= TOL_RGBA
     assert (r["rgba"][:, 3] > 0.5).mean() > 0.05  # the object is in view
 
@@ -78,6 +80,7 @@ def test_outdoor_3m_sampled():
     err, ndiv = compare_rgba(r["rgba"], cam, w.scene, w.options, pix=pix, gpu_sched=r["sched"],
                              gpu_sched_n=r["sched_n"], params=params)
     record_divergence("outdoor_3m", ndiv, len(pix))
+    record_parity("outdoor_3m, 256 px", "max-abs RGBA", err)
     assert err <= TOL_RGBA
 
 
@@ -88,7 +91,7 @@ def test_batched_views_sampled(name, per_cam, ncam_checked):
     assert r["status"] == 0
     offs = np.concatenate([[0], np.cumsum([c.n_rays for c in w.cameras])])
     params = oracle.Params(w.scene)
-    ndiv_all, n_all = 0, 0
+    ndiv_all, n_all, worst = 0, 0, 0.0
     for ci in range(0, len(w.cameras), max(1, len(w.cameras) // ncam_checked))[:ncam_checked]:
         cam = w.cameras[ci]
         pix = synth.pixel_subset(cam, per_cam, seed=100 + ci)
@@ -98,7 +101,9 @@ def test_batched_views_sampled(name, per_cam, ncam_checked):
         assert err <= TOL_RGBA
         ndiv_all += ndiv
         n_all += len(pix)
+        worst = max(worst, err)
     record_divergence(f"{name}, {ncam_checked} views", ndiv_all, n_all)
+    record_parity(f"{name}, {ncam_checked} views x {per_cam} px", "max-abs RGBA", worst)
     assert ndiv_all <= max(1, MAX_DIVERGENT_FRAC * n_all)
 
 

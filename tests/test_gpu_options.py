@@ -39,7 +39,7 @@ def test_zero_knobs_select_defaults_then_the_tuned_values():
     explicit = rgx.make_opts(dataclasses.replace(w.options, hit_cap=512, tile_w=32, tile_h=1, n_s=16))
     assert torch.equal(_render(sc, cams, zero), _render(sc, cams, explicit))
     best, _ = sc.autotune(cams, zero, tune_ns=True, with_backward=False)
-    assert best.hit_cap in (128, 192, 256, 384, 512, 640, 768) and best.n_s in (4, 8, 16, 32)
+    assert best.hit_cap in (32, 64, 96, 128, 192, 256, 384, 512, 640, 768) and best.n_s in (4, 8, 16, 32)
     tuned = rgx.make_opts(dataclasses.replace(w.options, hit_cap=best.hit_cap, tile_w=best.tile_w,
                                               tile_h=best.tile_h, n_s=best.n_s,
                                               lower_first=bool(best.flags & rgx.RGX_LOWER_FIRST)))

@@ -27,7 +27,7 @@ import torch
 import oracle
 from paper_2509_07782_b300 import autograd, rgx, synth
 from helpers import (TOL_GRAD, TOL_RGBA, compare_rgba, gpu_backward, gpu_render, rel_l2, schedules_agree,
-                     record_divergence)
+                     record_divergence, record_parity)
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +63,8 @@ def test_outdoor_3m_full_size_chunked_gradients():
     assert g["status"] == 0
     gr = oracle.backward(w.scene, cam, o, W, pix=pix, params=params)
     errs = {k: rel_l2(g[k], gr[k]) for k in NAMES}
+    record_parity("outdoor_3m full, hit_cap 128, 320 px", "max-abs RGBA", err)
+    record_parity("outdoor_3m full, hit_cap 128, 320 px", "worst gradient rel L2", max(errs.values()))
     for k in NAMES:
         assert np.linalg.norm(gr[k]) > 0, k
         assert errs[k] <= TOL_GRAD, f"{k}: rel L2 {errs[k]:.3g} ({errs})"
@@ -96,6 +98,7 @@ def test_batch_1m_one_launch_adjoint_matches_oracle_sum_over_views():
         for k in NAMES:
             total[k] = total[k] + gv[k]
     errs = {k: rel_l2(g[k], total[k]) for k in NAMES}
+    record_parity("batch_1m one-launch adjoint, 8 views x 24 px", "worst gradient rel L2", max(errs.values()))
     for k in NAMES:
         assert np.linalg.norm(total[k]) > 0, k
         assert errs[k] <= TOL_GRAD, f"{k}: rel L2 {errs[k]:.3g} ({errs})"
@@ -213,3 +216,48 @@ def test_tuned_segment_length_parity():
     for k in NAMES:
         e = rel_l2(g[k], gr[k])
         assert e <= TOL_GRAD, f"{k}: rel L2 {e:.3g}"
+
+
+def test_batch_1m_at_the_bench_knobs():
+    """The 8-view batch at the knobs its benchmark line tunes to (N_S = 32, hit_cap 32,
+    32x1 tiles; short lists, so the 168-register kernels run and almost every segment is
+    chunked and taken from the forward's sums records in the adjoint): forward and adjoint
+    against the oracle run at the same N_S."""
+    w = synth.workload("batch_1m")
+    o = dataclasses.replace(w.options, n_s=32, hit_cap=32, tile_w=32, tile_h=1)
+    r = gpu_render(w.scene, w.cameras, o, sched_cap=32)
+    assert r["status"] == 0
+    offs = np.concatenate([[0], np.cumsum([c.n_rays for c in w.cameras])])
+    params = oracle.Params(w.scene)
+    rng = np.random.default_rng(81)
+    d = np.zeros((int(offs[-1]), 4))
+    per_view = []
+    ndiv_all, n_all, worst = 0, 0, 0.0
+    for ci, cam in enumerate(w.cameras):
+        pix = synth.pixel_subset(cam, 24, seed=800 + ci)
+        sl = slice(offs[ci], offs[ci + 1])
+        err, ndiv = compare_rgba(r["rgba"][sl], cam, w.scene, o, pix=pix, gpu_sched=r["sched"][sl],
+                                 gpu_sched_n=r["sched_n"][sl], params=params)
+        assert err <= TOL_RGBA
+        ndiv_all += ndiv
+        n_all += len(pix)
+        worst = max(worst, err)
+        ref = oracle.render(w.scene, cam, o, pix=pix, sched_cap=32, params=params)
+        agree = schedules_agree(r["sched"][sl], r["sched_n"][sl], ref["sched"], ref["sched_n"], pix)
+        assert agree.mean() >= 0.95
+        W = _weights(rng, len(pix), agree)
+        d[offs[ci] + pix] = W
+        per_view.append((cam, pix, W))
+    record_divergence("batch_1m at N_S=32, hit_cap 32", ndiv_all, n_all)
+    g = gpu_backward(r, d)
+    assert g["status"] == 0
+    total = {k: 0.0 for k in NAMES}
+    for cam, pix, W in per_view:
+        gv = oracle.backward(w.scene, cam, o, W, pix=pix, params=params)
+        for k in NAMES:
+            total[k] = total[k] + gv[k]
+    errs = {k: rel_l2(g[k], total[k]) for k in NAMES}
+    record_parity("batch_1m at the bench knobs (N_S 32, hit_cap 32)", "max-abs RGBA", worst)
+    record_parity("batch_1m at the bench knobs (N_S 32, hit_cap 32)", "worst gradient rel L2", max(errs.values()))
+    for k in NAMES:
+        assert errs[k] <= TOL_GRAD, f"{k}: rel L2 {errs[k]:.3g}"
