@@ -66,6 +66,8 @@ SWEEP = ("sweep_6m: 6,000,000 torus Gaussians, 64 seeded views 256..1920 x 256..
 METRIC = "Mrays/s render & fwd+bwd ms/iter vs plain marcher at ≤1e-4 err; % HBM peak"
 # workloads whose autotuning includes N_S (the batched training step names all three knobs)
 TUNE_NS = {"batch_1m"}
+# seconds of oracle work the reference arm's timed steps take in all (its sample is sized to it)
+REF_BUDGET_S = 90.0
 
 
 def workload_label(name: str, fallback: str = "") -> str:
@@ -656,12 +658,24 @@ def reference_line(args):
     w = synth.workload(args.workload)
     P = oracle.Params(w.scene)
     cores = os.cpu_count() or 1
-    # the oracle brute-forces every Gaussian per ray: the sample shrinks with N
-    npix = int(min(2048, max(64, 2048 * 100_000 // max(w.scene.n, 1))))
     cams = w.cameras if args.workload != "sweep_6m" else w.cameras[:8]
-    per = max(1, npix // len(cams))
-    samples = [(cam, synth.pixel_subset(cam, min(per, cam.n_rays), seed=3 + i)) for i, cam in enumerate(cams)]
     with_bwd = args.workload != "sweep_6m"
+    # the oracle brute-forces every Gaussian per ray: the per-step sample is sized from its measured
+    # rate so that the timed steps take about REF_BUDGET_S seconds in all (at least one pixel per view)
+    # (one call with a pixel per core, so that every OpenMP thread works as in the timed steps)
+    # (a pixel per core of every view, one call per view: every OpenMP thread busy, as in the timed
+    # steps, whose per-view sample is a multiple of the core count where the budget allows)
+    probe = [(cam, synth.pixel_subset(cam, cores, seed=900 + i)) for i, cam in enumerate(cams)]
+    t0 = time.perf_counter()
+    for cam, pix in probe:
+        oracle.render(w.scene, cam, w.options, pix=pix, params=P, nthreads=cores)
+        if with_bwd:
+            oracle.backward(w.scene, cam, w.options, np.ones((len(pix), 4)), pix=pix, params=P, nthreads=cores)
+    dt_probe = max(time.perf_counter() - t0, 1e-6)  # seconds for `cores` pixels of every view
+    budget = REF_BUDGET_S / max(args.steps, 1)
+    per = cores * int(budget // dt_probe) if budget >= dt_probe else int(cores * budget / dt_probe)
+    per = int(min(max(per, 1), max(1, 2048 // len(cams))))
+    samples = [(cam, synth.pixel_subset(cam, min(per, cam.n_rays), seed=3 + i)) for i, cam in enumerate(cams)]
     Ws = [np.random.default_rng(4 + i).normal(size=(len(p), 4)) for i, (_, p) in enumerate(samples)]
     for _ in range(max(args.warmup, 0)):
         cam, pix = samples[0]
