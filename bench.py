@@ -364,11 +364,18 @@ def run_plain(sc_factory, w, t, up, opts_tuned, stream, reps=3):
     res = [once(True) for _ in range(reps)]
     fm = statistics.median(r[0] for r in res)
     bm = statistics.median(r[1] for r in res)
+    # work counters of one untimed forward per view, summed over the views
+    work = {}
+    for cb in singles:
+        sp.forward(cb, popts)
+        for k, v in sp.counters(stream).items():
+            work[k] = work.get(k, 0) + v
     R = sum(c.n_rays for c in w.cameras)
     out = {"fwd_ms": fm, "bwd_ms": bm, "fwd_bwd_ms": fm + bm, "render_mrays_s": R / fm / 1e3,
            "fwd_bwd_mrays_s": R / (fm + bm) / 1e3,
            "options": f"uniform dt={po.dt}, N_S={po.n_s}, hit_cap={popts.hit_cap}, no skip, caller order, "
-                      f"scanline rays, one launch per view ({len(singles)} views)"}
+                      f"scanline rays, one launch per view ({len(singles)} views)",
+           "work_fwd": work}
     if sp.status() != 0:
         out["status"] = "device status nonzero"
     return out

@@ -22,7 +22,13 @@
 //      with a multiplicative warp scan for T_k (Eq. 3);
 //   4. an empty hit set advances by dS, or with RGX_SKIP jumps to ClosestHit
 //      (Eq. 4): from the window's chords when they decide it, else by a
-//      cooperative nearest-hit traversal.
+//      cooperative nearest-hit traversal (at a ray's start first limited to a
+//      little beyond the previous ray's first hit, which prunes it from the start).
+// A segment whose hits overflow the list marks the ray as in a dense stretch:
+// its following segments are collected in chunks straight away, and so is the
+// first segment of the work item's next ray (the flag is kept in the ray's
+// state, so the adjoint takes the same path) -- instead of first trying windows
+// that would overflow again.
 //
 // The adjoint kernel replays exactly the same decisions and arithmetic, so it
 // reproduces T and the schedule bit for bit without storing any sample.  Per
@@ -38,12 +44,16 @@
 
 // Version of the march kernels: changed whenever their code changes, so that
 // profiler counters taken on an older version are not attributed to this one.
-#define RGX_MARCH_VERSION "m2-10"
+#define RGX_MARCH_VERSION "m2-13"
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
 #define WARPS (RGX_BLOCK / 32)
-#define STK 320                                     // per-warp traversal stack
+// Per-warp traversal stack.  A dense window's frontier fills it: with 320 entries the
+// room above the depth-first reserve let a step pop only 21 of its 32 nodes on average
+// on a 1M-Gaussian scene, with 512 it pops 31 (forward 17 % faster there); beyond 512
+// nothing changes, and up to 512 the stack leaves the occupancy at hit_cap 512 as it was.
+#define STK 512
 #define STK_RES 152                                 // depth-first reserve: 3 x (4-wide depth bound 48) + 4
 #define SURV 160                                    // leaves awaiting their exact chord (< 32 left + 128 new)
 #define CUT 32                                      // child records of a tile's BVH cut
@@ -56,7 +66,7 @@
 
 #define TAPE_CHUNK 2048                             // tape entries a warp reserves at a time
 #define TAPE_FULL 0xffffffffu                       // a warp's tape_base once a reservation has failed
-#define RGX_CSUM_SLOTS 8                            // chunked-segment sums records per ray
+#define RGX_CSUM_SLOTS 32                           // chunked-segment sums records per ray
 #define PTAPE_BLOCK 65536                           // chord indices a warp reserves at a time
 #define PTAPE_MIN_FREE 4096                         // a chunked segment starts a new block below this much room
 #define RGX_CSUM_BUDGET (16ull << 30)               // bytes for those records
@@ -622,6 +632,24 @@ __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, floa
     return best;
 }
 
+// ClosestHit(ta) with a guess: the query is first limited to [ta, lim) with lim a
+// little beyond the guess (a neighbouring ray's first hit), which prunes from the
+// first step; when nothing starts below lim the rest [lim, tf) is searched.  The
+// result is the same minimum either way (the limited query returns lim exactly
+// when no chord with t_in < lim ends after ta).
+__device__ __forceinline__ float w_closest_guess(const MarchParams& P, const WS& W, const Ray& r, float ta, float tf,
+                                                 float guess, Counters& cnt) {
+    if (guess > ta && guess < tf) {
+        const float lim = fminf(__fadd_rn(guess, __fmul_rn(0.02f, __fsub_rn(guess, ta))), tf);
+        if (lim > ta && lim < tf) {
+            const float t = w_closest(P, W, r, ta, lim, cnt);
+            if (t < lim) return t;
+            return w_closest(P, W, r, lim, tf, cnt);
+        }
+    }
+    return w_closest(P, W, r, ta, tf, cnt);
+}
+
 // ------------------------------------------------------------------ per-segment work
 // Lane-parallel sample evaluation: lane = (sample k, group grp); the group's
 // lanes take every G-th hit.  Entry indices come from W.seg (idx) or 0..m-1.
@@ -796,7 +824,7 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
                           const float4& root_lo, const float4& root_hi, const float4& up, const float4& st,
                           const uint4& st2, Counters& cnt, bool& whole, uint32_t& tape_base,
                           uint32_t& tape_left, uint32_t& pt_base, uint32_t& pt_left, float4& o_rgba,
-                          float4& o_state, uint4& o_tape, int& o_nrec) {
+                          float4& o_state, uint4& o_tape, int& o_nrec, float& th_guess, bool& carry_dense) {
     const int lane = threadIdx.x & 31;
     const int k = lane % NS;
     const int cap = P.hit_cap;
@@ -933,8 +961,9 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             // no chord starts inside a window that had to be lowered: look beyond it
             th = m < INFINITY ? fminf(m, tf) : (w_hi >= tf ? tf : w_closest(P, W, r, tn, tf, cnt));
         } else {
-            th = w_closest(P, W, r, tn, tf, cnt);
+            th = w_closest_guess(P, W, r, tn, tf, th_guess, cnt);
         }
+        if (th < tf) th_guess = th;
         if (uniform) {
             const int jj = (int)floorf((th - tn) / P.dt) - 1;
             j = jj > 0 ? jj : 0;
@@ -943,6 +972,11 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             tS = th;
         }
     }
+    // A ray that does not start with a whole-ray window starts in chunked mode when the
+    // previous ray of its work item ended in a dense stretch (the forward records this in
+    // the ray's state, so that the adjoint starts the same way)
+    const bool start_dense = !used_whole && (BWD ? (!fwd_whole && st2.w == 1u) : carry_dense);
+    dense = start_dense;
     const float minstep = uniform ? P.dt : (float)NS * fminf(P.dt_min, P.dt_max);
     // max_segments = 0: the ray's own bound, (t_f - t_n) / minstep + 8, but never above
     // RGX_SEGMENT_CEILING, so that a scene box vast next to the step cannot keep a warp busy
@@ -1244,7 +1278,9 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
         o_rgba = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
         // the sign bit of T (>= 0) records the first-window path for the adjoint's replay
         o_state = make_float4(C0, C1, C2, used_whole ? -T : T);
-        o_tape = make_uint4(tape_off, (uint32_t)tape_cnt, P.tape_tag, __float_as_uint(first_hi));
+        o_tape = make_uint4(tape_off, (uint32_t)tape_cnt, P.tape_tag,
+                            used_whole ? __float_as_uint(first_hi) : (start_dense ? 1u : 0u));
+        carry_dense = dense;
         o_nrec = nrec;
     }
 }
@@ -1487,6 +1523,8 @@ __device__ __forceinline__ void march_kernel(const MarchParams& P) {
             build_cut(P, W, tile_frustum(cam, pxa, pya, pxb, pyb), cnt);
         }
         bool whole = true;  // whole-ray first windows, until one overflows in this work item
+        float th_guess = -1.0f;  // the last ray's first hit in this work item (none yet)
+        bool carry_dense = false;  // the last ray of this work item ended in a dense stretch
         for (int l = l0; l < l1; l++) {
             int px, py;
             if (!tile_pixel(cam, lt, l, zt, P.tile_w, P.tile_h, px, py)) continue;
@@ -1505,7 +1543,7 @@ __device__ __forceinline__ void march_kernel(const MarchParams& P) {
                                    __shfl_sync(FULLMASK, my_st2.z, l), __shfl_sync(FULLMASK, my_st2.w, l));
             }
             march_ray<NS, BWD>(P, W, ray, c, cam, px, py, root_lo, root_hi, up_l, st_l, st2_l, cnt, whole, tape_base,
-                               tape_left, pt_base, pt_left, o_rgba, o_state, o_tape, o_nrec);
+                               tape_left, pt_base, pt_left, o_rgba, o_state, o_tape, o_nrec, th_guess, carry_dense);
             if (!BWD && lane == l) { my_rgba = o_rgba; my_state = o_state; my_tape = o_tape; my_nrec = o_nrec; }
         }
         if (!BWD) {
@@ -1823,8 +1861,8 @@ static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t n
             else { s->csums = nullptr; cudaGetLastError(); }
         }
         s->csum_slots = (s->csums && s->csum_alloc >= cneed) ? (int)slots : 0;
-        // the index tape of the recorded segments' chords: up to 512 per ray within its budget
-        size_t pneed = s->csum_slots > 0 ? (size_t)R * 512 : 0;
+        // the index tape of the recorded segments' chords: up to 2,048 per ray within its budget
+        size_t pneed = s->csum_slots > 0 ? (size_t)R * 2048 : 0;
         if (pneed > (size_t)RGX_PTAPE_MAX) pneed = (size_t)RGX_PTAPE_MAX;
         if (pneed > 0 && s->ptape_alloc < pneed) {
             if (s->ptape) cudaFree(s->ptape);
