@@ -16,6 +16,8 @@ Prints one JSON line (rank 0).  ``value`` is whole-job Mrays/s of the step
 with inputs resident in HBM, timed with CUDA events per replay on the graph's
 stream, L2 flushed (256 MiB write) between steps outside the events.  Events
 between the build, forward and adjoint graphs split each step into stages.
+The single-view ``torus_100k`` and ``outdoor_3m`` steps and the forward-only
+``sweep_6m`` ride along as sub-objects, each beside its plain marcher.
 ``e2e`` repeats the step through the C-ABI with host (pinned) buffers: every
 step uploads its parameters and upstream gradient and downloads its gradients
 and image inside the timed region.  ``plain_marcher`` times the plain
@@ -89,7 +91,7 @@ def parse(argv=None):
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-extras", action="store_true",
-                   help="leave out the torus_100k and sweep_6m sub-objects of the default line")
+                   help="leave out the torus_100k, outdoor_3m and sweep_6m sub-objects of the default line")
     p.add_argument("--no-tune", action="store_true", help="skip rgx_autotune (the workload's own knobs)")
     p.add_argument("--tune-exhaustive", action="store_true", help="rgx_autotune over the full candidate grid")
     p.add_argument("--tile", default=None, help="fixed ray-tile shape WxH (skips rgx_autotune)")
@@ -781,16 +783,18 @@ def main():
     r = run_step(args, args.workload, rank, world, local, plain=not args.no_plain, e2e=not args.no_e2e)
     extras = {}
     if rank == 0 and args.workload == WORKLOAD and not args.no_extras:
-        sub = parse(["--steps", "10", "--warmup", "3"])
-        c2 = run_step(sub, "torus_100k", 0, 1, local, plain=True, e2e=False)
-        extras["torus_100k"] = {"workload": workload_label("torus_100k"), "value": c2["value"], "unit": "Mrays/s",
-                                "ms_per_step": c2["ms_per_step"], "build_ms": c2["build_ms"], "fwd_ms": c2["fwd_ms"],
-                                "bwd_ms": c2["bwd_ms"], "render_mrays_s": c2["R"] / c2["fwd_ms"] / 1e3,
-                                "knobs": c2["tuned"], "plain_marcher": c2["plain"],
-                                "speedup_vs_plain": {"render": c2["plain"]["fwd_ms"] / c2["fwd_ms"],
-                                                     "fwd_bwd": c2["plain"]["fwd_bwd_ms"] /
-                                                     (c2["fwd_ms"] + c2["bwd_ms"])},
-                                "device_status": c2["status"]}
+        # the single-view workloads beside the batch: the sparse object view and the dense
+        # outdoor view, each with the plain marcher on the same view
+        for name, steps in (("torus_100k", "10"), ("outdoor_3m", "5")):
+            sub = parse(["--steps", steps, "--warmup", "3"])
+            c = run_step(sub, name, 0, 1, local, plain=True, e2e=False)
+            extras[name] = {"workload": workload_label(name), "value": c["value"], "unit": "Mrays/s",
+                            "steps": int(steps), "ms_per_step": c["ms_per_step"], "build_ms": c["build_ms"],
+                            "fwd_ms": c["fwd_ms"], "bwd_ms": c["bwd_ms"], "render_mrays_s": c["R"] / c["fwd_ms"] / 1e3,
+                            "knobs": c["tuned"], "plain_marcher": c["plain"],
+                            "speedup_vs_plain": {"render": c["plain"]["fwd_ms"] / c["fwd_ms"],
+                                                 "fwd_bwd": c["plain"]["fwd_bwd_ms"] / (c["fwd_ms"] + c["bwd_ms"])},
+                            "device_status": c["status"]}
         extras["sweep_6m"] = run_sweep(args, steps=2)
     if world > 1:
         import torch.distributed as dist

@@ -91,7 +91,7 @@ struct rgx_scene {
     size_t csum_alloc = 0;         // in float4
     int csum_slots = 0;            // records per ray the next forward with a state uses
     int csum_slots_last = 0, csum_ns_last = 0;  // layout of the last forward's records
-    uint32_t* ptape = nullptr;     // chord indices of recorded chunked segments
+    uint4* ptape = nullptr;        // chords of recorded chunked segments: (packed index, colour bits)
     size_t ptape_alloc = 0, ptape_cap = 0, ptape_cap_last = 0;  // entries: allocated / next forward / last forward
     // the last rgx_autotune result: what tuning knobs left at 0 select
     int has_tuned = 0;

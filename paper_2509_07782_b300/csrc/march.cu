@@ -44,7 +44,7 @@
 
 // Version of the march kernels: changed whenever their code changes, so that
 // profiler counters taken on an older version are not attributed to this one.
-#define RGX_MARCH_VERSION "m2-13"
+#define RGX_MARCH_VERSION "m2-14"
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
@@ -67,10 +67,13 @@
 #define TAPE_CHUNK 2048                             // tape entries a warp reserves at a time
 #define TAPE_FULL 0xffffffffu                       // a warp's tape_base once a reservation has failed
 #define RGX_CSUM_SLOTS 32                           // chunked-segment sums records per ray
-#define PTAPE_BLOCK 65536                           // chord indices a warp reserves at a time
+#define PTAPE_BLOCK 65536                           // index-tape entries a warp reserves at a time
+#ifndef PTAPE_STORE
+#define PTAPE_STORE(p, v) (*(p) = (v))
+#endif
 #define PTAPE_MIN_FREE 4096                         // a chunked segment starts a new block below this much room
 #define RGX_CSUM_BUDGET (16ull << 30)               // bytes for those records
-#define RGX_PTAPE_MAX (4000000000ull)               // entries of the index tape at most (16 GB; 32-bit offsets)
+#define RGX_PTAPE_MAX (3000000000ull)               // entries of the index tape at most (48 GB with their colours)
 
 struct MarchParams {
     const float4* __restrict__ geom;
@@ -105,7 +108,8 @@ struct MarchParams {
     float4* csums;       // per (ray, chunked segment ordinal < csum_slots): N_S + 1 float4 -- the segment's
                          // per-sample sums (sigma, S) as composited, then (hit count bits, 0, 0, 0)
     uint32_t csum_slots; // records per ray (0: none)
-    uint32_t* ptape;     // packed indices of recorded chunked segments' chords, in the order the forward met them
+    uint4* ptape;        // recorded chunked segments' chords in the order the forward met them: (packed index,
+                         // colour R, G, B bits) -- the colour as the forward evaluated it
     uint32_t* ptape_n;   // forward: entries reserved so far (per-warp blocks of PTAPE_BLOCK)
     uint32_t ptape_cap;  // capacity in entries (0: none)
     float2* sched;
@@ -1098,7 +1102,12 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
                 eval_entries<NS>(W, false, m, tS, dtk, true, sig, S0, S1, S2);
                 if (!BWD && pt_ok) {
                     if ((uint32_t)(tot + m) <= pt_left) {
-                        for (int e = lane; e < m; e += 32) P.ptape[pt_base + (uint32_t)tot + e] = W.pid[e];
+                        for (int e = lane; e < m; e += 32) {
+                            const float4 c = W.c[e];
+                            PTAPE_STORE(&P.ptape[(size_t)pt_base + (uint32_t)tot + e],
+                                        make_uint4(W.pid[e], __float_as_uint(c.y), __float_as_uint(c.z),
+                                                   __float_as_uint(c.w)));
+                        }
                     } else {
                         pt_ok = false;
                     }
@@ -1245,14 +1254,14 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
                 for (int b = 0; b < nexact; b += cap) {
                     const int m = min(cap, nexact - b);
                     for (int e = lane; e < m; e += 32) {
-                        const uint32_t q = P.ptape[pid_off + (uint32_t)(b + e)];
-                        const Chord ch = chord_of(P.geom, q, r);
+                        // the index and the forward's colour bits: no SH record gathered again
+                        const uint4 x = P.ptape[(size_t)pid_off + (uint32_t)(b + e)];
+                        const Chord ch = chord_of(P.geom, x.x, r);
                         W.q[e] = make_float4(ch.tc, ch.a, ch.qmin, ch.Qe);
-                        W.c[e] = make_float4(ch.L, 0.f, 0.f, 0.f);
-                        W.pid[e] = q;
+                        W.c[e] = make_float4(ch.L, __uint_as_float(x.y), __uint_as_float(x.z), __uint_as_float(x.w));
+                        W.pid[e] = x.x;
                     }
                     __syncwarp();
-                    colour_entries(P, W, r, 0, m);
                     adjoint_flush<NS>(P, W, r, false, m, tS, dtk, 0, NS, cam);
                 }
             } else {
@@ -1861,14 +1870,15 @@ static rgx_status forward_common(rgx_scene* s, const rgx_camera* cams, int32_t n
             else { s->csums = nullptr; cudaGetLastError(); }
         }
         s->csum_slots = (s->csums && s->csum_alloc >= cneed) ? (int)slots : 0;
-        // the index tape of the recorded segments' chords: up to 2,048 per ray within its budget
+        // the index tape of the recorded segments' chords, each with its colour (16 B an entry): up to
+        // 2,048 per ray within its budget
         size_t pneed = s->csum_slots > 0 ? (size_t)R * 2048 : 0;
         if (pneed > (size_t)RGX_PTAPE_MAX) pneed = (size_t)RGX_PTAPE_MAX;
         if (pneed > 0 && s->ptape_alloc < pneed) {
             if (s->ptape) cudaFree(s->ptape);
             s->ptape = nullptr;
             s->ptape_alloc = 0;
-            if (cudaMalloc(&s->ptape, pneed * sizeof(uint32_t)) == cudaSuccess) s->ptape_alloc = pneed;
+            if (cudaMalloc(&s->ptape, pneed * sizeof(uint4)) == cudaSuccess) s->ptape_alloc = pneed;
             else { s->ptape = nullptr; cudaGetLastError(); }
         }
         s->ptape_cap = (s->ptape && s->ptape_alloc >= pneed) ? pneed : 0;
