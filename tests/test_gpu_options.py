@@ -8,7 +8,9 @@
   RGX_ERR_ITER_LIMIT, in bounded time, instead of marching to the box's exit;
 * the forward's tape of first chord lists may be capped or disabled
   (rgx_set_tape_limit): rays whose lists find no room are collected again by
-  the adjoint, and the gradients do not change.
+  the adjoint, and the gradients do not change -- on a sparse view (first chord
+  lists) and on a dense one (the sums records and the index tape with colours
+  of chunked segments).
 """
 import dataclasses
 import time
@@ -98,3 +100,35 @@ def test_tape_limit_leaves_gradients_unchanged(limit):
     cnt = sc.counters()
     # without room on the tape the adjoint collected the lists itself
     assert cnt["node_visits"] > 0
+
+
+def test_dense_view_records_and_taped_colours_leave_gradients_unchanged():
+    """A dense view (segments overflow a 32-entry list and are collected in chunks): the
+    adjoint that reads the forward's sums records and its index tape -- each chunked chord's
+    packed index with the colour the forward evaluated -- gives the gradients of the adjoint
+    that collects, evaluates and colours every chunked segment itself (tape disabled), to
+    rounding, with far fewer node visits; the forward image does not depend on the tape."""
+    w = synth.workload("batch_1m", n=400_000)
+    cam = synth.rescale_camera(w.cameras[3], 0.25)  # 256 x 192 of the 1024 x 768 view
+    o = dataclasses.replace(w.options, hit_cap=32, n_s=32, tile_w=32, tile_h=1)
+    d = np.random.default_rng(11).normal(size=(cam.n_rays, 4))
+    ref = gpu_render(w.scene, [cam], o)
+    assert ref["status"] == 0
+    ref_fwd = ref["scene"].counters()
+    g_ref = gpu_backward(ref, d)
+    assert g_ref["status"] == 0
+    taped = ref["scene"].counters()
+    sc = rgx.Scene()
+    sc.set_tape_limit(0)
+    r = gpu_render(w.scene, [cam], o, scene_obj=sc)
+    assert r["status"] == 0
+    assert np.array_equal(r["rgba"], ref["rgba"])
+    g = gpu_backward(r, d)
+    assert g["status"] == 0
+    untaped = sc.counters()
+    # the view is dense: its segments average several lists of hits
+    assert ref_fwd["hits"] > 4 * 32 * ref_fwd["segments"]
+    for k in ("means", "scales", "quats", "densities", "sh"):
+        scale = np.abs(g_ref[k]).max() + 1e-30
+        assert np.abs(g[k] - g_ref[k]).max() <= 1e-4 * scale, k
+    assert taped["node_visits"] < 0.5 * untaped["node_visits"]
