@@ -614,9 +614,32 @@ def run_sweep(args, steps=None):
     dev = torch.device("cuda", 0)
     steps = steps or args.steps
     w = synth.workload("sweep_6m")
-    opts = rgx.make_opts(w.options)   # the workload's own knobs (8x4 tiles, hit_cap 256): not tuned here
+    wo = w.options
     t = rgx.scene_tensors(w.scene, device=dev)
     sc = rgx.Scene(0)
+    if args.tile or args.hit_cap or args.n_s:
+        if args.tile:
+            wo.tile_w, wo.tile_h = (int(x) for x in args.tile.lower().split("x"))
+        if args.hit_cap:
+            wo.hit_cap = args.hit_cap
+        if args.n_s:
+            wo.n_s = args.n_s
+        opts = rgx.make_opts(wo)
+        knobs = {"tile": [wo.tile_w, wo.tile_h], "hit_cap": wo.hit_cap, "n_s": wo.n_s, "fixed": True}
+    elif args.no_tune:
+        opts = rgx.make_opts(wo)
+        knobs = {"tile": [wo.tile_w, wo.tile_h], "hit_cap": wo.hit_cap, "n_s": wo.n_s, "tuned": False}
+    else:
+        # rgx_autotune (forward only) on every 8th view: a sample of the sizes in one launch
+        sc.build(*t, rgx.make_opts(wo))
+        sub = rgx.Cameras(w.cameras[::8])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        opts, best_ms = sc.autotune(sub, rgx.make_opts(wo), tune_ns=True, with_backward=False)
+        knobs = {"tile": [opts.tile_w, opts.tile_h], "hit_cap": opts.hit_cap, "n_s": opts.n_s,
+                 "lower_first": bool(opts.flags & 32), "tuned_knobs": "tile shape, hit_cap, N_S, first-window lowering",
+                 "tuned_on": f"every 8th view ({len(w.cameras[::8])} of {len(w.cameras)}), forward only",
+                 "best_candidate_ms": best_ms, "tuning_wall_ms": (time.perf_counter() - t0) * 1e3}
     sc.build(*t, opts)
     cams_all = rgx.Cameras(w.cameras)
     singles = [rgx.Cameras([c]) for c in w.cameras]
@@ -645,12 +668,14 @@ def run_sweep(args, steps=None):
     q = [fps[0], fps[len(fps) // 2], fps[-1]]
     peaks, src = load_peaks()
     # forward only: no gradient tells which Gaussians were read, so all of them count (an upper bound)
+    kname = f"k_march<{int(opts.n_s)},0>"
     hbm = hbm_roofline(w.scene.n, cams_all.n_rays, ms_persistent / 1e3, False, float(peaks.get("hbm_gbs", 6400.0)),
-                       ray_bytes=16)
-    hbm.update(kernel="k_march<16,0>", peak_source=f"{src} copy bandwidth",
+                       traffic=profiled_traffic(kname, "sweep_6m"), ray_bytes=16)
+    hbm.update(kernel=kname, peak_source=f"{src} copy bandwidth",
                touched_note="every Gaussian counted as read (upper bound; forward only)")
     return {"workload": SWEEP, "rays_per_step": cams_all.n_rays, "render_mrays_s": cams_all.n_rays / ms_persistent / 1e3,
             "ms_per_render": ms_persistent, "steps": steps,
+            "knobs": knobs,
             "one_launch_per_view": {"ms_total": ms_per_view_total,
                                     "mrays_s": cams_all.n_rays / ms_per_view_total / 1e3},
             "fps_per_view": {"smallest": {"pixels": q[0][0], "fps": q[0][1]},
