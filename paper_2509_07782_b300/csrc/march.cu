@@ -44,16 +44,16 @@
 
 // Version of the march kernels: changed whenever their code changes, so that
 // profiler counters taken on an older version are not attributed to this one.
-#define RGX_MARCH_VERSION "m2-14"
+#define RGX_MARCH_VERSION "m2-15"
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
 #define WARPS (RGX_BLOCK / 32)
 // Per-warp traversal stack.  A dense window's frontier fills it: with 320 entries the
 // room above the depth-first reserve let a step pop only 21 of its 32 nodes on average
-// on a 1M-Gaussian scene, with 512 it pops 31 (forward 17 % faster there); beyond 512
-// nothing changes, and up to 512 the stack leaves the occupancy at hit_cap 512 as it was.
-#define STK 512
+// on a 1M-Gaussian scene, with 448-1,024 about 31 (forward 17 % faster there).  448 is
+// the most that still lets eight adjoint warps of hit_cap 512 share an SM's shared memory.
+#define STK 448
 #define STK_RES 152                                 // depth-first reserve: 3 x (4-wide depth bound 48) + 4
 #define SURV 160                                    // leaves awaiting their exact chord (< 32 left + 128 new)
 #define CUT 32                                      // child records of a tile's BVH cut
@@ -643,15 +643,20 @@ __device__ float w_closest(const MarchParams& P, const WS& W, const Ray& r, floa
 // when no chord with t_in < lim ends after ta).
 __device__ __forceinline__ float w_closest_guess(const MarchParams& P, const WS& W, const Ray& r, float ta, float tf,
                                                  float guess, Counters& cnt) {
+    float hi = tf;
     if (guess > ta && guess < tf) {
         const float lim = fminf(__fadd_rn(guess, __fmul_rn(0.02f, __fsub_rn(guess, ta))), tf);
-        if (lim > ta && lim < tf) {
-            const float t = w_closest(P, W, r, ta, lim, cnt);
-            if (t < lim) return t;
-            return w_closest(P, W, r, lim, tf, cnt);
-        }
+        if (lim > ta && lim < tf) hi = lim;
     }
-    return w_closest(P, W, r, ta, tf, cnt);
+    // one call site, two passes at most: [ta, lim), then [lim, tf) when nothing starts below lim
+    float lo = ta, t;
+    while (true) {
+        t = w_closest(P, W, r, lo, hi, cnt);
+        if (t < hi || hi >= tf) break;
+        lo = hi;
+        hi = tf;
+    }
+    return t;
 }
 
 // ------------------------------------------------------------------ per-segment work
