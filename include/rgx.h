@@ -165,7 +165,15 @@ rgx_status rgx_build_bvh_sg(rgx_scene* scene, int64_t n, int32_t sh_degree,
  *                           tape holds its first chord list.  The tape (scene
  *                           workspace, hit_cap / 6 entries of 48 B per ray) keeps the
  *                           lists of the LAST forward call only; an adjoint given
- *                           the state of an older call collects them again
+ *                           the state of an older call collects them again.  With a
+ *                           state the forward also records, for up to 32 segments per
+ *                           ray whose chords overflow hit_cap, the segment's per-sample
+ *                           sums ((N_S + 1) x 16 B, within 16 GB) and its chords in the
+ *                           order met, each as its packed index and the colour it
+ *                           evaluated (16 B, up to 2,048 per ray, within 48 GB); the
+ *                           adjoint reads them instead of traversing and colouring
+ *                           again.  Workspace that cannot be allocated is simply not
+ *                           used (same results, more work)
  */
 rgx_status rgx_render_forward(rgx_scene* scene, const rgx_camera* cams, int32_t ncam,
                               const rgx_opts* opts, float* rgba, void* fwd_state, void* stream);
@@ -283,9 +291,10 @@ rgx_status rgx_densify_accumulate(int64_t n, const float* means, const float* d_
  * Cap the forward's tape (the finished first chord lists the adjoint reads back
  * instead of traversing again; 48 B per entry, by default hit_cap / 6 entries per
  * ray, e.g. 29 GB for 7.1 M rays at hit_cap 512) at max_entries entries; 0
- * disables the tape, a negative value restores the default sizing.  Results do
- * not depend on it: rays whose lists find no room are collected again by the
- * adjoint.  Takes effect at the next rgx_render_forward with a state.
+ * disables the tape and the records of overflowing segments, a negative value
+ * restores the default sizing.  Results do not depend on it: rays whose lists
+ * find no room are collected again by the adjoint.  Takes effect at the next
+ * rgx_render_forward with a state.
  */
 rgx_status rgx_set_tape_limit(rgx_scene* scene, int64_t max_entries);
 

@@ -68,9 +68,6 @@
 #define TAPE_FULL 0xffffffffu                       // a warp's tape_base once a reservation has failed
 #define RGX_CSUM_SLOTS 32                           // chunked-segment sums records per ray
 #define PTAPE_BLOCK 65536                           // index-tape entries a warp reserves at a time
-#ifndef PTAPE_STORE
-#define PTAPE_STORE(p, v) (*(p) = (v))
-#endif
 #define PTAPE_MIN_FREE 4096                         // a chunked segment starts a new block below this much room
 #define RGX_CSUM_BUDGET (16ull << 30)               // bytes for those records
 #define RGX_PTAPE_MAX (3000000000ull)               // entries of the index tape at most (48 GB with their colours)
@@ -1109,9 +1106,8 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
                     if ((uint32_t)(tot + m) <= pt_left) {
                         for (int e = lane; e < m; e += 32) {
                             const float4 c = W.c[e];
-                            PTAPE_STORE(&P.ptape[(size_t)pt_base + (uint32_t)tot + e],
-                                        make_uint4(W.pid[e], __float_as_uint(c.y), __float_as_uint(c.z),
-                                                   __float_as_uint(c.w)));
+                            P.ptape[(size_t)pt_base + (uint32_t)tot + e] =
+                                make_uint4(W.pid[e], __float_as_uint(c.y), __float_as_uint(c.z), __float_as_uint(c.w));
                         }
                     } else {
                         pt_ok = false;
