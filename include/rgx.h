@@ -367,7 +367,8 @@ rgx_status rgx_densify_apply(int64_t n, const int32_t* action, const int32_t* of
 rgx_status rgx_sync_status(rgx_scene* scene, void* stream);
 
 /* Bytes of per-ray state written by rgx_render_forward (32: C[3], T, the collection path, tape offset,
- * count and tag, and the first window's end or whether the ray started in a dense stretch). */
+ * count and tag, and the first window's end -- or, for a ray without a whole-ray first window, its
+ * ClosestHit(t_n) and whether it started in a dense stretch). */
 size_t rgx_fwd_state_bytes(void);
 
 /* Static description of the last error on this scene (or globally if NULL). */

@@ -44,7 +44,7 @@
 
 // Version of the march kernels: changed whenever their code changes, so that
 // profiler counters taken on an older version are not attributed to this one.
-#define RGX_MARCH_VERSION "m2-15"
+#define RGX_MARCH_VERSION "m2-16"
 #define FULLMASK 0xffffffffu
 #define LEAF_BIT 0x80000000u
 #define NEG_HALF_LOG2E (-0.72134752044448170368f)   // -1 / (2 ln 2)
@@ -874,6 +874,8 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
     const bool csum_ok = BWD && P.csums != nullptr && P.csum_slots > 0 && st2.z == P.tape_tag;
     uint32_t tape_off = 0;
     int tape_cnt = -1;  // forward: where this ray's first-window list went on the tape (-1: not taped)
+    float th_start = 0.0f;  // ClosestHit(t_n) of a ray without a whole-ray window (kept in its state)
+    bool query = false;     // ClosestHit(t_n) still to be found by a nearest-hit traversal
     float wlen = 4.0f * (float)NS * (uniform ? P.dt : P.dt_max);
     if (P.n > 0 && tf > tn && skip) {
         // One window over the whole ray [t_n, t_f): when every chord fits in the
@@ -965,10 +967,17 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
             for (int e = lane; e < nL; e += 32) m = fminf(m, fmaxf(W.tio[e].x, tn));
             m = warp_min(m);
             // no chord starts inside a window that had to be lowered: look beyond it
-            th = m < INFINITY ? fminf(m, tf) : (w_hi >= tf ? tf : w_closest(P, W, r, tn, tf, cnt));
+            if (m < INFINITY) th = fminf(m, tf);
+            else if (w_hi >= tf) th = tf;
+            else query = true;
+        } else if (BWD && st2.y == 0xffffffffu) {
+            // the forward's ClosestHit(t_n) of this ray, kept in its state: no query again
+            th = __uint_as_float(st2.x);
         } else {
-            th = w_closest_guess(P, W, r, tn, tf, th_guess, cnt);
+            query = true;
         }
+        if (query) th = w_closest_guess(P, W, r, tn, tf, th_guess, cnt);  // the one call site at a ray's start
+        if (!have) th_start = th;
         if (th < tf) th_guess = th;
         if (uniform) {
             const int jj = (int)floorf((th - tn) / P.dt) - 1;
@@ -1288,7 +1297,9 @@ __device__ void march_ray(const MarchParams& P, const WS& W, int64_t ray, int ca
         o_rgba = make_float4(C0 + T * P.bg0, C1 + T * P.bg1, C2 + T * P.bg2, 1.0f - T);
         // the sign bit of T (>= 0) records the first-window path for the adjoint's replay
         o_state = make_float4(C0, C1, C2, used_whole ? -T : T);
-        o_tape = make_uint4(tape_off, (uint32_t)tape_cnt, P.tape_tag,
+        // a ray with a whole-ray window keeps where its list is on the tape and the window's end; one
+        // without keeps its ClosestHit(t_n) and whether it started in a dense stretch
+        o_tape = make_uint4(used_whole ? tape_off : __float_as_uint(th_start), (uint32_t)tape_cnt, P.tape_tag,
                             used_whole ? __float_as_uint(first_hi) : (start_dense ? 1u : 0u));
         carry_dense = dense;
         o_nrec = nrec;
