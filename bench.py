@@ -748,7 +748,8 @@ def step_line(args, r, world):
     k_s = (r["bwd_ms"] if dominant_is_bwd else r["fwd_ms"]) / 1e3
     flops = flops_b if dominant_is_bwd else flops_f
     achieved = flops / k_s / 1e12
-    traffic = profiled_traffic(kname, args.workload)
+    # ncu's DRAM bytes describe the full-size workload: none for a scaled-down view
+    traffic = profiled_traffic(kname, args.workload) if not args.scale_res else None
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": traffic,
                 "peak_source": f"derived (not measured): 148 SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz; "
