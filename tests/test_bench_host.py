@@ -140,3 +140,27 @@ def test_clock_sampler_summarises_rows_and_reasons():
     assert c["sm_mhz"] == 2032.0 and c["sm_max_mhz"] == 2032.0
     assert c["reasons"] == ["hw_slowdown", "sw_power_cap"]
     assert c["samples"] == 4
+
+
+def test_step_line_attaches_profiled_traffic_only_at_full_size(monkeypatch, tmp_path):
+    """The DRAM bytes ncu counted describe the full-size workload: a line built on
+    views scaled down for a profiler's small case carries none."""
+    import types
+    src = tmp_path / "paper_2509_07782_b300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "march.cu").write_text('#define RGX_MARCH_VERSION "v9"\n')
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "b.md").write_text(
+        "traffic_bytes_per_launch batch_1m k_march<32,0> 1000000 kernel_version v9\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    cnt = {"evals": 10_000, "hits": 100, "segments": 10, "rays": 50}
+    r = dict(R=50, ncam=1, ms_per_step=3.0, value=1.0, build_ms=0.1, fwd_ms=2.0, bwd_ms=1.0, e2e=None,
+             counters_fwd=cnt, counters_bwd=cnt, clocks={}, status=0, plain=None, opts=types.SimpleNamespace(n_s=32),
+             tuned={}, n=10, n_touched=10, steps_launches=21)
+    full = bench.step_line(bench.parse(["--workload", "batch_1m"]), r, 1)
+    assert full["roofline"]["kernel"] == "k_march<32,0>"
+    assert full["roofline"]["traffic"] == 1_000_000
+    assert full["hbm_roofline"]["dram_bytes"] == 1_000_000
+    small = bench.step_line(bench.parse(["--workload", "batch_1m", "--scale-res", "0.12"]), r, 1)
+    assert small["roofline"]["traffic"] is None and "dram_bytes" not in small["hbm_roofline"]
+    assert "scaled by 0.12" in small["config"]["workload"]
