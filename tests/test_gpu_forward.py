@@ -84,9 +84,15 @@ def test_outdoor_3m_sampled():
     assert err <= TOL_RGBA
 
 
-@pytest.mark.parametrize("name,per_cam,ncam_checked", [("batch_1m", 48, 8), ("sweep_6m", 24, 4)])
-def test_batched_views_sampled(name, per_cam, ncam_checked):
+# the sweep at the knobs bench.py times it with (rgx_autotune's pick on every 8th view: 32x1 tiles, hit_cap 64)
+@pytest.mark.parametrize("name,per_cam,ncam_checked,knobs", [
+    ("batch_1m", 48, 8, {}),
+    ("sweep_6m", 24, 4, dict(tile_w=32, tile_h=1, hit_cap=64, n_s=16)),
+])
+def test_batched_views_sampled(name, per_cam, ncam_checked, knobs):
+    import dataclasses
     w = synth.workload(name)
+    w = dataclasses.replace(w, options=dataclasses.replace(w.options, **knobs))
     r = gpu_render(w.scene, w.cameras, w.options, sched_cap=48)
     assert r["status"] == 0
     offs = np.concatenate([[0], np.cumsum([c.n_rays for c in w.cameras])])
